@@ -160,8 +160,10 @@ static double orc_uniform_pm1(uint64_t seed, uint64_t i)
 /* ---------------------------------------------------------------- inverse iteration */
 /* Tridiagonal Gaussian elimination with partial pivoting of A = T - lambda I
  * (textbook).  U has a diagonal u0 and two superdiagonals u1, u2; mult[i] and
- * swap[i] record the elimination of row i+1.  Exact zero pivots are replaced by
- * tiny (so the solve amplifies the eigenvector direction instead of failing). */
+ * swap[i] record the elimination of row i+1.  Pivots smaller in magnitude than tiny
+ * (eps ||T||_1) are replaced by +-tiny, keeping their sign, so the solve amplifies the
+ * eigenvector direction instead of overflowing (e.g. a denormal pivot when lambda is an
+ * eigenvalue next to zero). */
 static void orc_tri_lu(int n, const double *d, const double *e, double lambda, double tiny,
                        double *u0, double *u1, double *u2, double *mult, int *swp)
 {
@@ -181,7 +183,7 @@ static void orc_tri_lu(int n, const double *d, const double *e, double lambda, d
         } else {
             swp[i] = 0;
         }
-        if (r0 == 0.0) r0 = tiny;
+        if (fabs(r0) < tiny) r0 = (r0 < 0.0) ? -tiny : tiny;
         double m = s0 / r0;
         mult[i] = m;
         u0[i] = r0;
@@ -191,7 +193,7 @@ static void orc_tri_lu(int n, const double *d, const double *e, double lambda, d
         r1 = s2 - m * r2;
         r2 = 0.0;
     }
-    if (r0 == 0.0) r0 = tiny;
+    if (fabs(r0) < tiny) r0 = (r0 < 0.0) ? -tiny : tiny;
     u0[n - 1] = r0;
     u1[n - 1] = 0.0;
     u2[n - 1] = 0.0;

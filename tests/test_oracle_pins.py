@@ -167,3 +167,15 @@ def test_count_le_value_range():
     assert oracle.count_le(d, e, -6.5) == 1
     lo, hi = oracle.index_range(d, e, "V", vl=-6.5, vu=2.5)
     assert (lo, hi) == (2, 6)
+
+
+@pytest.mark.parametrize("n", [11, 101, 501])
+def test_clement_vectors_with_zero_eigenvalue(n):
+    # odd Clement matrices have the eigenvalue 0, which bisection resolves to a denormal;
+    # the inverse iteration must still return finite, orthonormal eigenvectors
+    d, e = tm.clement(n)
+    w = oracle.eigvals(d, e)
+    Z = oracle.eigvecs(d, e, w)
+    assert np.all(np.isfinite(Z))
+    assert M.scaled_residual(d, e, w, Z, n - 1.0) <= 10
+    assert M.scaled_orthogonality(Z) <= 10
