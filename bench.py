@@ -1,0 +1,343 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 MRRR path: eigenpairs/s for all eigenpairs of n = 8192 FP64
+symmetric tridiagonals (one 1-2-1, one Wilkinson W+ and one uniform(-1,1) matrix per
+step), with a live roofline of the dominant kernel, the CPU oracle timed beside it, an
+end-to-end number through the host-buffer C-ABI call, and SM clocks sampled during the
+timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mr3|reference] [--config c2]
+
+Under torchrun (N > 1) every rank solves its own copy of the step's matrices (the
+problems are independent: weak scaling, no collective on the data path); the time is
+the maximum over ranks.  `--impl reference` times the CPU oracle (bisection + inverse
+iteration) on a bounded sample of the same workload, on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import testmats as tm  # noqa: E402
+
+EPS = 2.0 ** -53
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 pipe of a GB300: 152 SMs x 2 DFMA/clk (measured: 1.19 TFLOP/s at 1995 MHz) x 2 flop
+# x 2070 MHz maximum SM clock.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+CONFIGS = {
+    "c1": {"workload": "plain MRRR, n=1000 uniform(-1,1) d and e, all eigenpairs, FP64",
+           "mats": [("random", 1000, (101, 102))]},
+    "c2": {"workload": "plain MRRR, n=8192 FP64, all eigenpairs, one matrix of each type per "
+                       "step: 1-2-1 (d=2, e=-1), Wilkinson W+ (d_i=|i-(n-1)/2|, e=1), "
+                       "uniform(-1,1) random d and e",
+           "mats": [("one_two_one", 8192, None), ("wilkinson", 8192, None),
+                    ("random", 8192, (201, 202))]},
+}
+
+
+def _matrices(cfg):
+    out = []
+    for kind, n, seeds in CONFIGS[cfg]["mats"]:
+        if kind == "random":
+            d, e = tm.random_uniform(n, *seeds)
+        else:
+            d, e = tm.make(kind, n)
+        out.append((kind, d, e))
+    return out
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clk", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sms, maxs, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sms.append(float(p[1]))
+                maxs.append(float(p[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if p[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sms) if sms else None,
+                "sm_max_mhz": max(maxs) if maxs else None, "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+# ------------------------------------------------------------------ CPU oracle legs
+
+def oracle_sample(mats, per_matrix):
+    """Oracle eigenpairs for `per_matrix` consecutive indices from the middle of each
+    matrix's spectrum; returns (eigenpairs, seconds)."""
+    import oracle
+    t0 = time.perf_counter()
+    count = 0
+    for _, d, e in mats:
+        n = len(d)
+        il = max(1, n // 2 - per_matrix // 2)
+        iu = min(n, il + per_matrix - 1)
+        w = oracle.eigvals(d, e, il, iu)
+        oracle.eigvecs(d, e, w)
+        count += iu - il + 1
+    return count, time.perf_counter() - t0
+
+
+def calibrate_sample(mats, budget_s):
+    per = 16
+    while True:
+        cnt, dt = oracle_sample(mats, per)
+        if dt * 2.2 > budget_s or per >= 4096:
+            return per, cnt, dt
+        per *= 2
+
+
+def cpu_baseline(mats, budget_s=15.0):
+    per, cnt, dt = calibrate_sample(mats, budget_s)
+    return {"value": cnt / dt, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle",
+            "sample": "%d consecutive mid-spectrum eigenpairs of each of the %d matrices "
+                      "(bisection to full accuracy + inverse iteration with MGS), %.1f s, "
+                      "single thread" % (per, len(mats), dt)}
+
+
+def run_reference(args, cfg, rank):
+    if rank != 0:
+        return
+    mats = _matrices(cfg)
+    budget = max(2.0, 150.0 / (args.steps + args.warmup))
+    per, _, _ = calibrate_sample(mats, budget)
+    for _ in range(args.warmup):
+        oracle_sample(mats, per)
+    tot_cnt, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        c, t = oracle_sample(mats, per)
+        tot_cnt += c
+        tot_t += t
+    value = tot_cnt / tot_t
+    line = {"impl": "reference", "metric": "eigenpairs/s (n=8192 all, FP64)", "value": value,
+            "unit": "eigenpairs/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": CONFIGS[cfg]["workload"],
+                                            "sample_per_matrix": per},
+            "cpu_baseline": {"value": value, "unit": "eigenpairs/s", "cores": 1,
+                             "kind": "oracle",
+                             "sample": "%d mid-spectrum eigenpairs per matrix per step" % per},
+            "e2e": {"value": value, "unit": "eigenpairs/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU leg
+
+def run_gpu(args, cfg, rank, world):
+    import torch
+    import paper_1401_4950_gb300 as mr3
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    mats = _matrices(cfg)
+    dev_mats = [(k, torch.tensor(d, device=dev), torch.tensor(e, device=dev)) for k, d, e in mats]
+    units_per_step = sum(len(d) for _, d, _ in mats)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    opts = mr3.make_opts(profile=1)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        infos = []
+        for _, d, e in dev_mats:
+            _, _, info = mr3.stemr(d, e, opts=opts)
+            infos.append(info)
+        return infos
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    agg = {"kernel_ms": np.zeros(8), "kernel_launches": np.zeros(8, dtype=np.int64),
+           "sturm_steps": 0, "shift_steps": 0, "twisted_steps": 0}
+    last_infos = None
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))  # L2 (129 MB) flushed between timed steps
+        ev[k][0].record(stream)
+        infos = step()
+        ev[k][1].record(stream)
+        for inf in infos:
+            agg["kernel_ms"] += np.array(inf["kernel_ms"])
+            agg["kernel_launches"] += np.array(inf["kernel_launches"])
+            for key in ("sturm_steps", "shift_steps", "twisted_steps"):
+                agg[key] += inf[key]
+        last_infos = infos
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([tot_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    ms_per_step = tot_ms / args.steps
+    value = world * units_per_step / (ms_per_step / 1e3)
+
+    # ---- dominant kernel and its roofline (FP64 pipe)
+    g = agg["kernel_ms"]
+    groups = {"k_bisect": (g[2] + g[6], agg["kernel_launches"][2] + agg["kernel_launches"][6],
+                           5.0 * agg["sturm_steps"]),
+              "k_rqi": (g[4], agg["kernel_launches"][4], 15.0 * agg["twisted_steps"]),
+              "k_shift": (g[5], agg["kernel_launches"][5], 5.0 * agg["shift_steps"])}
+    dom = max(groups, key=lambda k: groups[k][0])
+    ms, launches, flops = groups[dom]
+    achieved = (flops / max(launches, 1)) / (ms / max(launches, 1) / 1e3) / 1e12 if ms > 0 else 0.0
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "FP64 pipe: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                "kernel_share": float(ms / max(g.sum(), 1e-9))}
+
+    # ---- end to end through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if rank == 0 or True:
+        hbuf = []
+        nmax = max(len(d) for _, d, _ in mats)
+        Zh = torch.empty((nmax, nmax), dtype=torch.float64, pin_memory=True).numpy()
+        wh = torch.empty(nmax, dtype=torch.float64, pin_memory=True).numpy()
+        for _, d, e in mats:
+            dh = torch.empty(len(d), dtype=torch.float64, pin_memory=True).numpy()
+            eh = torch.empty(max(len(e), 1), dtype=torch.float64, pin_memory=True).numpy()
+            dh[:] = d
+            eh[: len(e)] = e
+            hbuf.append((dh, eh))
+        import ctypes
+        L = mr3.lib()
+
+        def e2e_step():
+            for dh, eh in hbuf:
+                n = len(dh)
+                m = ctypes.c_int(0)
+                rc = L.mr3_stemr_host(n, dh.ctypes.data_as(ctypes.c_void_p),
+                                      eh.ctypes.data_as(ctypes.c_void_p), 0, 0.0, 0.0, 1, n,
+                                      ctypes.byref(m), wh.ctypes.data_as(ctypes.c_void_p),
+                                      Zh.ctypes.data_as(ctypes.c_void_p), n, None, None,
+                                      ctypes.c_void_p(stream.cuda_stream))
+                assert rc in (0, 1, 2), rc
+        e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ne = max(2, min(args.steps, 5))
+        for _ in range(ne):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / ne
+        h2d = sum(8 * (len(d) + len(e)) for _, d, e in mats)
+        d2h = sum(8 * (len(d) + len(d) * len(d)) for _, d, _ in mats)
+        e2e = {"value": world * units_per_step / e2e_s, "unit": "eigenpairs/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(mats, budget_s=args.cpu_budget)
+    info0 = last_infos[0] if last_infos else {}
+    line = {"metric": "eigenpairs/s (n=8192 all, FP64)", "value": value, "unit": "eigenpairs/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": CONFIGS[cfg]["workload"],
+                       "n": [len(d) for _, d, _ in mats],
+                       "matrices_per_step": len(mats), "l2": "flushed between steps "
+                       "(256 MiB device write outside the per-step events)",
+                       "parallelism": "replicas, one set of matrices per GPU"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(agg["kernel_launches"].sum()),
+            "clocks": clk, "wall_s": wall,
+            "per_matrix": [dict(kind=k, **{key: inf[key] for key in (
+                "dmax", "largest_cluster", "nclusters", "new_rrr", "untested_rrr", "rqi_iters",
+                "rqi_iters_max", "bisect_fallbacks", "sturm_steps", "shift_steps",
+                "twisted_steps", "status")},
+                kernel_ms=[round(x, 3) for x in inf["kernel_ms"]])
+                for (k, _, _), inf in zip(mats, last_infos or [])],
+            "step_ms": [round(x, 3) for x in step_ms]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mr3", choices=["mr3", "reference"])
+    ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, args.config, rank)
+        return
+    run_gpu(args, args.config, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,201 @@
+/*
+ * mr3.h -- C ABI of the GB300 MRRR library (libmr3.so).
+ *
+ * The library computes eigenpairs (lambda_i, z_i) of a real symmetric tridiagonal
+ * matrix T = tridiag(e, d, e) with the method of Multiple Relatively Robust
+ * Representations (MRRR): the problem statement of the thesis' Alg. "MRRR"
+ * (Sec. 3.1.2): input T by its diagonal and off-diagonal, an index set or value
+ * interval; output eigenvalues and orthonormal eigenvectors.  The role matches
+ * LAPACK's xSTEMR (App. A).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - All floating-point data are IEEE binary64 (double).
+ *  - "device" pointers are CUDA device (or managed) memory of the current device;
+ *    "host" pointers are ordinary host memory (pinned memory is faster).
+ *  - Matrices are column-major.  Z holds one eigenvector per column.
+ *  - Eigenvalues are returned in ascending order; column j of Z belongs to w[j].
+ *  - Each eigenvector has unit 2-norm and an entry of largest magnitude is positive
+ *    (entries equal in magnitude in exact arithmetic are ordered by rounding).
+ *  - The caller owns every array; the library never frees caller memory.  The
+ *    library takes its internal workspace with stream-ordered allocation
+ *    (cudaMallocAsync) on the given stream and returns it before the call ends.
+ *  - stream is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *    All device work is enqueued on it.  The solver calls read a few counters back
+ *    to the host and therefore synchronise with the stream before returning; the
+ *    results are complete when the call returns.
+ *  - Return value: 0 on success; -i when argument i (1-based) is invalid; a
+ *    positive MR3_S* status when the result was produced but a safeguard fired
+ *    (see mr3_info.status_counts); MR3_EOOM / MR3_ECUDA on resource errors.
+ *  - Nothing here allocates or reads host memory passed as "device" or vice versa.
+ */
+#ifndef MR3_H
+#define MR3_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Which eigenpairs to compute (App. A / Sec. 3.2.1 remark 2). */
+typedef enum {
+    MR3_RANGE_ALL = 0,   /* all n eigenpairs                                  */
+    MR3_RANGE_VALUE = 1, /* eigenvalues in the half-open interval (vl, vu]    */
+    MR3_RANGE_INDEX = 2  /* eigenvalues il..iu (1-based, ascending)           */
+} mr3_range;
+
+/* Internal arithmetic of the representation tree (Ch. 5: FP64 in and out, the
+ * tree either in FP64 or in double-double). */
+typedef enum { MR3_FP64 = 0, MR3_DD = 1 } mr3_precision;
+
+/* Options; a zero-initialised struct (or NULL) selects the defaults in brackets. */
+typedef struct {
+    int prec;                  /* mr3_precision [MR3_FP64]                                   */
+    double gaptol;             /* classification threshold on reldist (Sec. 3.2.3)
+                                  [1e-3 for FP64, 1e-10 for DD (Ch. 5, Eq. gaptolinterval)] */
+    unsigned long long seed;   /* stream of the root's random perturbation (Alg. MRRR line 2)
+                                  [0x5EED]                                                   */
+    int max_rqi;               /* Rayleigh-quotient iterations per singleton before the
+                                  bisection fallback (Alg. S-task) [10]                      */
+    int max_shift_tries;       /* back-off steps per side when shifting a cluster
+                                  (Alg. "Shifting the spectrum") [8]                        */
+    unsigned fault_mask;       /* MR3_FAULT_* bits: host-selected fault injection [0]        */
+    int tpe;                   /* bisection lanes per eigenvalue: 0 = auto, else 1..32       */
+    int max_depth;             /* cap on the representation-tree depth [64]                  */
+    int profile;               /* nonzero: time each kernel group with CUDA events on the
+                                  call's stream and report it in mr3_info.kernel_ms [0]        */
+    int reserved[5];
+} mr3_opts;
+
+/* Fault injection (tests of the safeguards; nothing here faults a GPU). */
+#define MR3_FAULT_RQI_NOCONV   0x1u /* RQI never accepts: forces the bisection fallback   */
+#define MR3_FAULT_SHIFT_REJECT 0x2u /* every shifted representation fails the growth test */
+#define MR3_FAULT_NAN_SHIFT    0x4u /* the first shift candidate of each cluster is NaN   */
+
+/* Algorithmic status codes (positive return values) and their counters. */
+#define MR3_SOK             0
+#define MR3_SUNTESTED_RRR   1 /* a cluster representation was accepted untested (least growth) */
+#define MR3_SCAP            2 /* an iteration cap was hit for some eigenpair              */
+#define MR3_SNONFINITE      3 /* non-finite input                                         */
+#define MR3_SDEPTH          4 /* the tree depth cap was reached                           */
+#define MR3_EOOM            5 /* out of device memory                                     */
+#define MR3_ECUDA           6 /* a CUDA call failed                                       */
+#define MR3_ENOSCRATCH      7 /* request exceeds a fixed-size internal buffer             */
+
+/* Statistics of one call (Sec. 2.5 and Ch. 5 measures). */
+typedef struct {
+    int m;                     /* eigenpairs computed                                     */
+    int nblocks;               /* irreducible blocks after splitting (Sec. 3.2.1)         */
+    int dmax;                  /* depth of the representation tree (Sec. 3.1.2)           */
+    int nclusters;             /* cluster nodes processed                                 */
+    int largest_cluster;       /* size of the largest cluster (clustering rho * n, Ch. 5) */
+    int new_rrr;               /* representations computed for clusters                   */
+    int untested_rrr;          /* of those, accepted by least growth only (phi, Ch. 5)    */
+    long long rqi_iters;       /* Rayleigh-quotient iterations, summed                    */
+    int rqi_iters_max;         /* ... maximum over eigenpairs                             */
+    int bisect_fallbacks;      /* singletons finished by bisection + one Getvec           */
+    long long sturm_steps;     /* Sturm-count steps of the bisection kernel (work measure) */
+    long long shift_steps;     /* recurrence steps of the cluster-shift kernel              */
+    long long twisted_steps;   /* recurrence steps inside the singleton (RQI) kernel        */
+    int status_counts[8];      /* occurrences of each MR3_S* code                          */
+    /* With opts->profile: device time (ms) and launches per kernel group, measured with
+       CUDA events on the call's stream.  Groups: 0 prologue (norms, splitting, ranges),
+       1 root representation, 2 bisection on the root, 3 classification, 4 singletons (RQI),
+       5 cluster shifts, 6 refinement on child representations, 7 output ordering. */
+    double kernel_ms[8];
+    int kernel_launches[8];
+} mr3_info;
+
+/*
+ * mr3_stemr -- selected eigenpairs of one symmetric tridiagonal matrix.
+ *
+ *  n      (1)  order of T, n >= 0.
+ *  d      (2)  device, n doubles: diagonal alpha_1..alpha_n.
+ *  e      (3)  device, n-1 doubles: off-diagonal beta_1..beta_{n-1} (may be NULL if n <= 1).
+ *  range  (4)  mr3_range.
+ *  vl, vu (5,6) MR3_RANGE_VALUE: interval (vl, vu], vl < vu.  Ignored otherwise.
+ *  il, iu (7,8) MR3_RANGE_INDEX: 1 <= il <= iu <= n (or il = 1, iu = 0 when n = 0).
+ *  m      (9)  host int, out: number of eigenpairs found.
+ *  w      (10) device, out: m ascending eigenvalues (room for n when range = VALUE).
+ *  Z      (11) device, out: n x m column-major, leading dimension ldz.
+ *  ldz    (12) ldz >= max(1, n).
+ *  opts   (13) host, may be NULL.
+ *  info   (14) host, out, may be NULL.
+ *  stream (15) cudaStream_t as void*.
+ * Splitting (Sec. 3.2.1): off-diagonals with |beta_i| <= eps sqrt(n) ||T|| are
+ * treated as zero and each block is solved on its own; rows of a column outside
+ * its block are zero.
+ */
+int mr3_stemr(int n, const double *d, const double *e, int range, double vl, double vu,
+              int il, int iu, int *m, double *w, double *Z, int ldz,
+              const mr3_opts *opts, mr3_info *info, void *stream);
+
+/*
+ * mr3_stemr_host -- mr3_stemr on host arrays: the library copies d and e to the
+ * device, solves, and copies w (m values) and Z (n x m, leading dimension ldz) back
+ * into the caller's host arrays before returning.  Arguments as for mr3_stemr with
+ * host pointers.
+ */
+int mr3_stemr_host(int n, const double *d, const double *e, int range, double vl, double vu,
+                   int il, int iu, int *m, double *w, double *Z, int ldz,
+                   const mr3_opts *opts, mr3_info *info, void *stream);
+
+/*
+ * mr3_stemr_batched -- eigenpairs of nb independent tridiagonals of uneven sizes.
+ *
+ *  nb     (1)  number of matrices, nb >= 0.
+ *  n_off  (2)  host, nb+1 int64: matrix b has order n_b = n_off[b+1]-n_off[b] >= 0 and
+ *              occupies d[n_off[b] .. n_off[b+1]) and e[n_off[b] .. n_off[b+1]-1).
+ *  d      (3)  device, n_off[nb] doubles (packed diagonals).
+ *  e      (4)  device, n_off[nb] doubles (packed off-diagonals; the last slot of
+ *              each matrix is not read).
+ *  range  (5)  mr3_range, the same for every matrix.
+ *  vl, vu (6,7) host, nb doubles each (range VALUE), else may be NULL.
+ *  il, iu (8,9) host, nb ints each (range INDEX), else may be NULL.
+ *  m      (10) host, out, nb ints: eigenpairs found per matrix.
+ *  w      (11) device, out: eigenvalues of matrix b at w[n_off[b] ..] (room for n_b).
+ *  z_off  (12) host, nb int64: Z_b starts at Z + z_off[b] and is n_b x n_b
+ *              column-major with leading dimension n_b (room for n_b columns).
+ *  Z      (13) device, out.
+ *  opts   (14), info (15) as for mr3_stemr (info sums over the batch), stream (16).
+ */
+int mr3_stemr_batched(int nb, const long long *n_off, const double *d, const double *e,
+                      int range, const double *vl, const double *vu, const int *il,
+                      const int *iu, int *m, double *w, const long long *z_off, double *Z,
+                      const mr3_opts *opts, mr3_info *info, void *stream);
+
+/*
+ * mr3_backward -- gradient of a scalar loss L(lambda, Z) with respect to d and e,
+ * given the forward eigen-decomposition of T (all n eigenpairs) and the upstream
+ * gradients g = dL/dlambda and G = dL/dZ.
+ *
+ *   dbar_j = sum_i g_i z_ij^2 + Abar_jj,   ebar_j = 2 sum_i g_i z_ij z_i,j+1 + Abar_j,j+1 + Abar_j+1,j
+ *   Abar   = Z (F o (Z^T G)) Z^T  with  F_ik = 1/(lambda_k - lambda_i) (i != k), F_ii = 0,
+ *            regularised as (lambda_k - lambda_i)/((lambda_k - lambda_i)^2 + delta^2),
+ *            delta = n eps ||T|| (pairs closer than the solver can resolve).
+ *
+ *  n      (1)  order, n >= 0;  k (2) number of eigenpairs in w/Z: must equal n when G
+ *              is given; any 0 <= k <= n when G is NULL (eigenvalue part only).
+ *  w      (3)  device, k eigenvalues (ascending).
+ *  Z      (4)  device, n x k, leading dimension ldz (5) >= max(1, n).
+ *  gw     (6)  device, k doubles, or NULL (treated as 0).
+ *  gZ     (7)  device, n x k, leading dimension ldgz (8), or NULL (treated as 0).
+ *  dd     (9)  device, out, n doubles;  de (10) device, out, n-1 doubles.
+ *  opts   (11) may be NULL;  stream (12).
+ */
+int mr3_backward(int n, int k, const double *w, const double *Z, int ldz, const double *gw,
+                 const double *gZ, int ldgz, double *dd, double *de, const mr3_opts *opts,
+                 void *stream);
+
+/* Message for a return code (static string). */
+const char *mr3_strerror(int code);
+
+/* Library version string, e.g. "mr3-gb300 0.1 sm_103a". */
+const char *mr3_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MR3_H */

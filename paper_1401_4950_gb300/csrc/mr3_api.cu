@@ -1,0 +1,528 @@
+// mr3_api.cu -- C ABI entry points and the host side of the solver: argument checks,
+// workspace, and the level-by-level traversal of the representation tree (Alg. MRRR,
+// breadth first: per level classify, singletons by RQI, clusters by a shift and a
+// refinement on the child representation).
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+#include "mr3.h"
+#include "mr3_kernels.h"
+
+namespace mr3 {
+
+namespace {
+
+struct Opts {
+    int prec;
+    double gaptol;
+    unsigned long long seed;
+    int max_rqi;
+    int max_tries;
+    unsigned fault_mask;
+    int tpe;
+    int max_depth;
+    int profile;
+};
+
+Opts resolve(const mr3_opts *o) {
+    Opts r;
+    r.prec = (o && o->prec == MR3_DD) ? MR3_DD : MR3_FP64;
+    r.gaptol = (o && o->gaptol > 0.0) ? o->gaptol : (r.prec == MR3_DD ? 1e-10 : 1e-3);
+    r.seed = (o && o->seed) ? o->seed : 0x5EEDull;
+    r.max_rqi = (o && o->max_rqi > 0) ? o->max_rqi : 10;
+    r.max_tries = (o && o->max_shift_tries > 0) ? o->max_shift_tries : 8;
+    r.fault_mask = o ? o->fault_mask : 0u;
+    r.tpe = o ? o->tpe : 0;
+    r.max_depth = (o && o->max_depth > 0) ? o->max_depth : 64;
+    r.profile = o ? o->profile : 0;
+    return r;
+}
+
+// Lanes per eigenvalue for the multisection: enough lanes in flight to keep the SMs busy
+// (about 12 warps per SM on 152 SMs), at most 32; opts->tpe overrides.
+int lanes_for(long long nactive, const Opts &o) {
+    if (o.tpe > 0) {
+        int L = 1;
+        while (L * 2 <= o.tpe && L < 32) L *= 2;
+        return L;
+    }
+    const long long target = 152ll * 32 * 12;
+    int L = 1;
+    while (L < 32 && (long long)(2 * L) * nactive <= target) L *= 2;
+    return L;
+}
+
+// Optional per-group device timing: an event pair around every launch group, on the
+// call's stream; durations are read after the final synchronisation.
+struct Prof {
+    bool on;
+    cudaStream_t s;
+    std::vector<cudaEvent_t> evs;
+    std::vector<int> group;
+    std::vector<int> nlaunch;
+    explicit Prof(bool enabled, cudaStream_t st) : on(enabled), s(st) {}
+    int begin() {
+        if (!on) return -1;
+        cudaEvent_t a;
+        cudaEventCreate(&a);
+        cudaEventRecord(a, s);
+        evs.push_back(a);
+        return (int)evs.size() - 1;
+    }
+    void end(int tok, int g, int launches) {
+        if (!on || tok < 0) return;
+        cudaEvent_t b;
+        cudaEventCreate(&b);
+        cudaEventRecord(b, s);
+        evs.push_back(b);
+        group.push_back(g);
+        nlaunch.push_back(launches);
+    }
+    void collect(mr3_info &out) {
+        if (!on) return;
+        for (size_t k = 0; k < group.size(); ++k) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, evs[2 * k], evs[2 * k + 1]);
+            out.kernel_ms[group[k]] += ms;
+            out.kernel_launches[group[k]] += nlaunch[k];
+        }
+    }
+    ~Prof() {
+        for (auto e : evs) cudaEventDestroy(e);
+    }
+};
+
+// Stream-ordered workspace: every block is returned (cudaFreeAsync) when the call ends.
+struct Workspace {
+    cudaStream_t s;
+    std::vector<void *> blocks;
+    bool oom = false;
+    explicit Workspace(cudaStream_t st) : s(st) {}
+    template <class T> T *get(size_t count) {
+        void *p = nullptr;
+        const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+        if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+            cudaGetLastError();
+            oom = true;
+            return nullptr;
+        }
+        blocks.push_back(p);
+        return (T *)p;
+    }
+    void release(void *p) {
+        if (!p) return;
+        auto it = std::find(blocks.begin(), blocks.end(), p);
+        if (it != blocks.end()) {
+            cudaFreeAsync(p, s);
+            blocks.erase(it);
+        }
+    }
+    ~Workspace() {
+        for (void *p : blocks) cudaFreeAsync(p, s);
+    }
+};
+
+#define CK(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            cudaGetLastError();                                                          \
+            return (e_ == cudaErrorMemoryAllocation) ? MR3_EOOM : MR3_ECUDA;             \
+        }                                                                                \
+    } while (0)
+#define CKW(ws)                                                                          \
+    do {                                                                                 \
+        if ((ws).oom) return MR3_EOOM;                                                   \
+    } while (0)
+
+// The solver proper, for nmat matrices described by host MatDesc entries (off, n, zoff,
+// ldz, woff and the range data filled in).  ncols: size of the global column space.
+// On return mats[b].m holds the eigenpairs of matrix b.
+int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols,
+          const double *d, const double *e, int range, double *w, double *Z, const Opts &o,
+          mr3_info *info, cudaStream_t s) {
+    Workspace ws(s);
+    mr3_info out;
+    std::memset(&out, 0, sizeof(out));
+    if (nrows == 0 || nmat == 0) {
+        for (auto &M : mats) M.m = 0;
+        if (info) *info = out;
+        return 0;
+    }
+    MatDesc *dmats = ws.get<MatDesc>(nmat);
+    DevInfo *dinfo = ws.get<DevInfo>(1);
+    int *dint = ws.get<int>(4); // [0] bad input, [1] number of blocks
+    int *flags = ws.get<int>(nrows);
+    int *scanned = ws.get<int>(nrows);
+    int *scan_tmp = ws.get<int>(scan_tmp_ints(nrows));
+    CKW(ws);
+    CK(cudaMemcpyAsync(dmats, mats.data(), sizeof(MatDesc) * nmat, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(dinfo, 0, sizeof(DevInfo), s));
+    CK(cudaMemsetAsync(dint, 0, 4 * sizeof(int), s));
+    Prof prof(o.profile != 0, s);
+    int tk = prof.begin();
+    launch_mat_norm(nmat, dmats, d, e, dint, s);
+    launch_split_flags(nmat, dmats, nrows, d, e, flags, s);
+    launch_exclusive_scan(flags, scanned, nrows, dint + 1, scan_tmp, s);
+    prof.end(tk, 0, 5);
+    int hint[4];
+    CK(cudaMemcpyAsync(hint, dint, sizeof(hint), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hint[0]) {
+        for (auto &M : mats) M.m = 0;
+        out.status_counts[MR3_SNONFINITE] = 1;
+        if (info) *info = out;
+        return MR3_SNONFINITE;
+    }
+    const int nblk = hint[1];
+    BlkDesc *blks = ws.get<BlkDesc>(nblk);
+    CKW(ws);
+    tk = prof.begin();
+    build_blocks(nrows, flags, scanned, dint + 1, nblk, nmat, dmats, blks, s);
+    launch_blk_setup(nblk, blks, nmat, dmats, d, e, range, s);
+    if (range == MR3_RANGE_INDEX) launch_index_multi(nmat, dmats, blks, d, e, s);
+    launch_assign_columns(nmat, dmats, blks, range, s);
+    prof.end(tk, 0, range == MR3_RANGE_INDEX ? 6 : 5);
+    CK(cudaMemcpyAsync(mats.data(), dmats, sizeof(MatDesc) * nmat, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    ws.release(flags);
+    ws.release(scanned);
+    ws.release(scan_tmp);
+    long long mtotal = 0;
+    int nmax = 1;
+    for (auto &M : mats) { mtotal += M.m; nmax = std::max(nmax, M.n); }
+    out.nblocks = nblk;
+    out.m = (int)std::min<long long>(mtotal, 0x7fffffff);
+    if (mtotal == 0) {
+        if (info) *info = out;
+        return 0;
+    }
+    // ---- root representations and level-0 intervals
+    double *pool0 = ws.get<double>((size_t)kRepStride * nrows);
+    int *grid = ws.get<int>(ncols + 64ll * nblk + 1);
+    float *f32 = ws.get<float>(2 * nrows);
+    Node *nodes0 = ws.get<Node>(nblk);
+    int *cnode = ws.get<int>(ncols);
+    int *jloc = ws.get<int>(ncols);
+    double *lo = ws.get<double>(ncols);
+    double *hi = ws.get<double>(ncols);
+    double *gapl = ws.get<double>(ncols);
+    double *gapr = ws.get<double>(ncols);
+    SingleItem *singles = ws.get<SingleItem>(ncols);
+    ClusterItem *clusters = ws.get<ClusterItem>(ncols / 2 + 1);
+    long long *crep = ws.get<long long>(ncols / 2 + 1);
+    LevelCounters *ctr = ws.get<LevelCounters>(1);
+    int *work = ws.get<int>(1);
+    CKW(ws);
+    CK(cudaMemsetAsync(cnode, 0xff, sizeof(int) * ncols, s));
+    tk = prof.begin();
+    launch_root(nblk, blks, d, e, pool0, f32, o.seed, s);
+    launch_init_columns(nblk, blks, nodes0, cnode, jloc, lo, hi, (int)ncols, s);
+    prof.end(tk, 1, 2);
+    const double rtol = 1e-2 * o.gaptol;
+    if (range != MR3_RANGE_ALL) launch_outer_gaps(nblk, blks, nodes0, pool0, rtol, dinfo, s);
+    bool any_multi = false;
+    for (auto &M : mats) any_multi |= (M.nblk > 1 && M.m > 0);
+    if (any_multi) launch_zero_z(nmat, dmats, Z, s);
+    tk = prof.begin();
+    {
+        int max_m = 0;
+        for (auto &M : mats) max_m = std::max(max_m, M.m);
+        launch_grid(nblk, blks, nodes0, pool0, grid, lo, hi, max_m, dinfo, s);
+        launch_bisect((int)ncols, nullptr, lanes_for(mtotal, o), (int)ncols, cnode, nodes0, blks,
+                      pool0, jloc, lo, hi, rtol, nullptr, dinfo, s);
+    }
+    prof.end(tk, 2, 3);
+    ws.release(f32);
+
+    // ---- level loop
+    Node *cur_nodes = nodes0;
+    double *cur_pool = pool0;
+    int ncur = nblk;
+    double *scratch = nullptr;
+    long long scratch_slots = 0;
+    const long long scratch_cap_bytes = 1ll << 30; // RQI scratch budget per launch
+    int status = 0;
+    for (int level = 0;; ++level) {
+        CK(cudaMemsetAsync(ctr, 0, sizeof(LevelCounters), s));
+        tk = prof.begin();
+        launch_classify(ncur, cur_nodes, blks, lo, hi, o.gaptol, gapl, gapr, singles, clusters,
+                        crep, cnode, ctr, dinfo, s);
+        prof.end(tk, 3, 1);
+        LevelCounters hc;
+        CK(cudaMemcpyAsync(&hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (hc.nsingle > 0) {
+            long long want = (hc.nsingle + 31) / 32;
+            const long long per_slot = 96ll * nmax * (long long)sizeof(double);
+            long long cap = std::max<long long>(152, scratch_cap_bytes / per_slot);
+            long long slots = std::min(want, cap);
+            slots = (slots + 3) / 4 * 4;
+            if (slots > scratch_slots) {
+                ws.release(scratch);
+                scratch = ws.get<double>((size_t)slots * 96 * nmax);
+                CKW(ws);
+                scratch_slots = slots;
+            }
+            tk = prof.begin();
+            launch_rqi(hc.nsingle, singles, cur_nodes, blks, dmats, cur_pool, jloc, lo, hi, gapl,
+                       gapr, d, e, w, Z, scratch, (int)slots, nmax, o.max_rqi, o.fault_mask, work,
+                       dinfo, s);
+            prof.end(tk, 4, 1);
+        }
+        if (hc.ncluster == 0) break;
+        const bool at_cap = (level + 1 >= o.max_depth);
+        double *next_pool = ws.get<double>((size_t)hc.pool_need);
+        Node *next_nodes = ws.get<Node>(hc.ncluster);
+        double *tau = ws.get<double>(hc.ncluster);
+        int *next_active = ws.get<int>(hc.nactive);
+        CKW(ws);
+        tk = prof.begin();
+        launch_shift(hc.ncluster, clusters, crep, cur_nodes, blks, cur_pool, next_pool,
+                     next_nodes, tau, cnode, next_active, jloc, lo, hi, o.max_tries, o.fault_mask,
+                     dinfo, s);
+        prof.end(tk, 5, 1);
+        tk = prof.begin();
+        launch_bisect(hc.nactive, next_active, lanes_for(hc.nactive, o), (int)ncols, cnode,
+                      next_nodes, blks, next_pool, jloc, lo, hi, rtol, tau, dinfo, s);
+        prof.end(tk, 6, 1);
+        ws.release(next_active);
+        if (cur_pool != pool0) ws.release(cur_pool);
+        if (cur_nodes != nodes0) ws.release(cur_nodes);
+        cur_pool = next_pool;
+        cur_nodes = next_nodes;
+        ncur = hc.ncluster;
+        if (at_cap) {
+            // Depth cap: the remaining cluster members are finished as singletons of their
+            // current representation (accuracy no longer guaranteed; flagged).
+            status = MR3_SDEPTH;
+            CK(cudaMemsetAsync(ctr, 0, sizeof(LevelCounters), s));
+            launch_classify(ncur, cur_nodes, blks, lo, hi, -1e308, gapl, gapr, singles, clusters,
+                            crep, cnode, ctr, dinfo, s);
+            CK(cudaMemcpyAsync(&hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (hc.nsingle > 0) {
+                long long slots = std::min<long long>((hc.nsingle + 31) / 32, std::max<long long>(152, scratch_cap_bytes / (96ll * nmax * 8)));
+                slots = (slots + 3) / 4 * 4;
+                if (slots > scratch_slots) {
+                    ws.release(scratch);
+                    scratch = ws.get<double>((size_t)slots * 96 * nmax);
+                    CKW(ws);
+                    scratch_slots = slots;
+                }
+                launch_rqi(hc.nsingle, singles, cur_nodes, blks, dmats, cur_pool, jloc, lo, hi,
+                           gapl, gapr, d, e, w, Z, scratch, (int)slots, nmax, o.max_rqi, o.fault_mask,
+                           work, dinfo, s);
+            }
+            break;
+        }
+    }
+    // ---- output order: sort the eigenpairs of matrices whose eigenvalues came out of order
+    int *oflags = ws.get<int>(nmat);
+    CKW(ws);
+    tk = prof.begin();
+    launch_order_flags(nmat, dmats, w, oflags, s);
+    prof.end(tk, 7, 1);
+    std::vector<int> hflags(nmat);
+    CK(cudaMemcpyAsync(hflags.data(), oflags, sizeof(int) * nmat, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int b = 0; b < nmat; ++b) {
+        const MatDesc &M = mats[b];
+        if (hflags[b] && M.m > 1) {
+            double *wtmp = ws.get<double>(M.m);
+            double *ztmp = ws.get<double>((size_t)M.m * M.n);
+            int *perm = ws.get<int>(M.m);
+            CKW(ws);
+            tk = prof.begin();
+            launch_sort_outputs(b, M.m, dmats, w, Z, wtmp, ztmp, perm, s);
+            prof.end(tk, 7, 3);
+        }
+    }
+    DevInfo hi_info;
+    CK(cudaMemcpyAsync(&hi_info, dinfo, sizeof(hi_info), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaGetLastError());
+    out.dmax = hi_info.dmax;
+    out.nclusters = hi_info.nclusters;
+    out.largest_cluster = hi_info.largest;
+    out.new_rrr = hi_info.new_rrr;
+    out.untested_rrr = hi_info.untested;
+    out.rqi_iters = (long long)hi_info.rqi_iters;
+    out.rqi_iters_max = hi_info.rqi_max;
+    out.bisect_fallbacks = hi_info.fallbacks;
+    out.sturm_steps = (long long)hi_info.sturm_steps;
+    out.shift_steps = (long long)hi_info.shift_steps;
+    prof.collect(out);
+    out.twisted_steps = (long long)hi_info.twisted_steps;
+    for (int k = 0; k < 8; ++k) out.status_counts[k] = hi_info.status[k];
+    if (status) out.status_counts[status] += 1;
+    if (info) *info = out;
+    if (status) return status;
+    if (hi_info.status[MR3_SCAP]) return MR3_SCAP;
+    if (hi_info.status[MR3_SUNTESTED_RRR]) return MR3_SUNTESTED_RRR;
+    return 0;
+}
+
+} // namespace
+} // namespace mr3
+
+using namespace mr3;
+
+extern "C" {
+
+int mr3_stemr(int n, const double *d, const double *e, int range, double vl, double vu, int il,
+              int iu, int *m, double *w, double *Z, int ldz, const mr3_opts *opts,
+              mr3_info *info, void *stream) {
+    if (n < 0) return -1;
+    if (n > 0 && !d) return -2;
+    if (n > 1 && !e) return -3;
+    if (range < MR3_RANGE_ALL || range > MR3_RANGE_INDEX) return -4;
+    if (range == MR3_RANGE_VALUE && !(vl < vu)) return -6;
+    if (range == MR3_RANGE_INDEX) {
+        if (n == 0) { if (!(il == 1 && iu == 0)) return -7; }
+        else {
+            if (il < 1 || il > n) return -7;
+            if (iu < il || iu > n) return -8;
+        }
+    }
+    if (!m) return -9;
+    if (n > 0 && !w) return -10;
+    if (n > 0 && !Z) return -11;
+    if (ldz < std::max(1, n)) return -12;
+    *m = 0;
+    if (n == 0) {
+        if (info) std::memset(info, 0, sizeof(*info));
+        return 0;
+    }
+    const Opts o = resolve(opts);
+    std::vector<MatDesc> mats(1);
+    std::memset(mats.data(), 0, sizeof(MatDesc));
+    mats[0].off = 0;
+    mats[0].n = n;
+    mats[0].zoff = 0;
+    mats[0].ldz = ldz;
+    mats[0].woff = 0;
+    mats[0].il = il;
+    mats[0].iu = iu;
+    mats[0].vl = vl;
+    mats[0].vu = vu;
+    const int rc = solve(1, mats, n, n, d, e, range, w, Z, o, info, (cudaStream_t)stream);
+    *m = mats[0].m;
+    return rc;
+}
+
+int mr3_stemr_host(int n, const double *d, const double *e, int range, double vl, double vu,
+                   int il, int iu, int *m, double *w, double *Z, int ldz, const mr3_opts *opts,
+                   mr3_info *info, void *stream) {
+    if (n < 0) return -1;
+    if (n > 0 && !d) return -2;
+    if (n > 1 && !e) return -3;
+    if (!m) return -9;
+    if (n > 0 && !w) return -10;
+    if (n > 0 && !Z) return -11;
+    if (ldz < std::max(1, n)) return -12;
+    *m = 0;
+    if (n == 0) return mr3_stemr(0, nullptr, nullptr, range, vl, vu, il, iu, m, nullptr, nullptr, 1, opts, info, stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    double *dd = nullptr, *de = nullptr, *dw = nullptr, *dz = nullptr;
+    int rc = 0;
+    if (cudaMallocAsync((void **)&dd, sizeof(double) * n, s) != cudaSuccess ||
+        cudaMallocAsync((void **)&de, sizeof(double) * std::max(1, n - 1), s) != cudaSuccess ||
+        cudaMallocAsync((void **)&dw, sizeof(double) * n, s) != cudaSuccess ||
+        cudaMallocAsync((void **)&dz, sizeof(double) * (size_t)n * n, s) != cudaSuccess) {
+        cudaGetLastError();
+        rc = MR3_EOOM;
+    }
+    if (!rc) {
+        cudaMemcpyAsync(dd, d, sizeof(double) * n, cudaMemcpyHostToDevice, s);
+        if (n > 1) cudaMemcpyAsync(de, e, sizeof(double) * (n - 1), cudaMemcpyHostToDevice, s);
+        rc = mr3_stemr(n, dd, de, range, vl, vu, il, iu, m, dw, dz, n, opts, info, stream);
+        if (rc >= 0 && *m > 0) {
+            cudaMemcpyAsync(w, dw, sizeof(double) * (*m), cudaMemcpyDeviceToHost, s);
+            cudaMemcpy2DAsync(Z, sizeof(double) * ldz, dz, sizeof(double) * n, sizeof(double) * n,
+                              *m, cudaMemcpyDeviceToHost, s);
+        }
+        if (cudaStreamSynchronize(s) != cudaSuccess) { cudaGetLastError(); rc = MR3_ECUDA; }
+    }
+    if (dd) cudaFreeAsync(dd, s);
+    if (de) cudaFreeAsync(de, s);
+    if (dw) cudaFreeAsync(dw, s);
+    if (dz) cudaFreeAsync(dz, s);
+    return rc;
+}
+
+int mr3_stemr_batched(int nb, const long long *n_off, const double *d, const double *e, int range,
+                      const double *vl, const double *vu, const int *il, const int *iu, int *m,
+                      double *w, const long long *z_off, double *Z, const mr3_opts *opts,
+                      mr3_info *info, void *stream) {
+    if (nb < 0) return -1;
+    if (nb > 0 && !n_off) return -2;
+    if (range < MR3_RANGE_ALL || range > MR3_RANGE_INDEX) return -5;
+    if (nb == 0) {
+        if (info) std::memset(info, 0, sizeof(*info));
+        return 0;
+    }
+    const long long nrows = n_off[nb] - n_off[0];
+    if (n_off[0] != 0) return -2;
+    for (int b = 0; b < nb; ++b)
+        if (n_off[b + 1] < n_off[b] || n_off[b + 1] - n_off[b] > 0x7fffffffll) return -2;
+    if (nrows > 0 && !d) return -3;
+    if (nrows > 0 && !e) return -4;
+    if (range == MR3_RANGE_VALUE) {
+        if (!vl) return -6;
+        if (!vu) return -7;
+        for (int b = 0; b < nb; ++b) if (!(vl[b] < vu[b])) return -7;
+    }
+    if (range == MR3_RANGE_INDEX) {
+        if (!il) return -8;
+        if (!iu) return -9;
+        for (int b = 0; b < nb; ++b) {
+            const long long nbk = n_off[b + 1] - n_off[b];
+            if (nbk == 0) continue;
+            if (il[b] < 1 || il[b] > nbk) return -8;
+            if (iu[b] < il[b] || iu[b] > nbk) return -9;
+        }
+    }
+    if (!m) return -10;
+    if (nrows > 0 && !w) return -11;
+    if (!z_off) return -12;
+    if (nrows > 0 && !Z) return -13;
+    const Opts o = resolve(opts);
+    std::vector<MatDesc> mats(nb);
+    for (int b = 0; b < nb; ++b) {
+        MatDesc &M = mats[b];
+        std::memset(&M, 0, sizeof(M));
+        M.off = n_off[b];
+        M.n = (int)(n_off[b + 1] - n_off[b]);
+        M.zoff = z_off[b];
+        M.ldz = std::max(1, M.n);
+        M.woff = (int)n_off[b];
+        M.il = il ? il[b] : 1;
+        M.iu = iu ? iu[b] : M.n;
+        M.vl = vl ? vl[b] : 0.0;
+        M.vu = vu ? vu[b] : 0.0;
+    }
+    const int rc = solve(nb, mats, nrows, nrows, d, e, range, w, Z, o, info, (cudaStream_t)stream);
+    for (int b = 0; b < nb; ++b) m[b] = mats[b].m;
+    return rc;
+}
+
+const char *mr3_strerror(int code) {
+    if (code < 0) return "invalid argument";
+    switch (code) {
+    case MR3_SOK: return "success";
+    case MR3_SUNTESTED_RRR: return "a cluster representation was accepted without passing the growth test";
+    case MR3_SCAP: return "an iteration cap was reached for some eigenpair";
+    case MR3_SNONFINITE: return "non-finite input";
+    case MR3_SDEPTH: return "representation tree depth cap reached";
+    case MR3_EOOM: return "out of device memory";
+    case MR3_ECUDA: return "CUDA error";
+    case MR3_ENOSCRATCH: return "request exceeds a fixed-size internal buffer";
+    default: return "unknown status";
+    }
+}
+
+const char *mr3_version(void) { return "mr3-gb300 0.1 sm_103a"; }
+
+} // extern "C"

@@ -1,0 +1,229 @@
+// mr3_internal.cuh -- data structures and device numerics shared by the MRRR kernels.
+//
+// Notation follows the thesis (Ch. 3): a representation is an N-representation of a
+// lower bidiagonal factorization L D L^T with d (n pivots) and l (n-1 multipliers);
+// the derived data dl_i = d_i l_i and dll_i = d_i l_i^2 are kept beside d (remark on
+// Alg. NegCount on LDL^T, App. B).  A representation of order n occupies kRepStride * n
+// doubles of a pool starting at an even double offset: d at [0, n), dl at [n, 2n), dll at
+// [2n, 3n), and from the even offset rep_df_offset(n) a double-float copy
+// {d.h, d.l, dll.h, dll.l} (one 16-byte aligned float4 per index) for the bisection.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mr3 {
+
+constexpr double kEps = 1.1102230246251565e-16;     // unit roundoff 2^-53
+constexpr double kSafmin = 2.2250738585072014e-308; // underflow threshold omega
+constexpr int kRepStride = 6;                       // doubles per index in a representation
+__host__ __device__ __forceinline__ long long rep_df_offset(int n) { return 3ll * n + (n & 1); }
+
+// One input matrix of a (possibly batched) solve.
+struct MatDesc {
+    long long off;  // first row in the packed d/e arrays
+    long long zoff; // Z element offset of the first eigenvector of this matrix
+    int n;          // order
+    int ldz;        // leading dimension of this matrix's Z
+    int woff;       // first global column (index into w and the per-column state)
+    int m;          // eigenpairs selected (set on the device)
+    int blk0, nblk; // blocks after splitting
+    int il, iu;     // index range (range INDEX), 1-based
+    double vl, vu;  // value range (range VALUE): (vl, vu]
+    double tnorm;   // max(|gl|, |gu|) of the Gershgorin interval of the whole matrix
+};
+
+// One irreducible block (Sec. 3.2.1): the unit the root representation is built for.
+struct BlkDesc {
+    long long off;  // first row in the packed d/e arrays
+    long long rep;  // offset of the root representation in the level-0 pool
+    int n;          // order
+    int mat;        // owning matrix
+    int roff;       // first row inside the matrix
+    int j0, j1;     // local eigenvalue indices selected (1-based, inclusive; j1 < j0: none)
+    int col0;       // global column of local index j0
+    int dfok;       // the root's double-float copy keeps full precision
+    double gl, gu;  // Gershgorin interval of the block
+    double mu;      // root shift: M_root = T_block - mu I (before the random perturbation)
+    double spdiam;  // gu - gl
+};
+
+// A node {M, I, sigma} of the representation tree (Alg. MRRR): a representation, a
+// contiguous range of global columns, and the accumulated shift.
+struct Node {
+    long long rep;     // offset of the representation in this level's pool
+    int blk;           // owning block
+    int c0, c1;        // global columns (inclusive)
+    int depth;
+    int dfok;          // the double-float copy keeps full precision (see df_safe)
+    double sigma;      // eigenvalue of T = eigenvalue of the representation + sigma
+    double lnb, rnb;   // bounds (in this representation's coordinates) of the nearest
+                       // eigenvalues outside [c0, c1]: upper bound of the left one, lower
+                       // bound of the right one; -inf / +inf when there is none
+};
+
+struct ClusterItem {
+    int node;          // parent node (current level)
+    int c0, c1;        // cluster columns
+    int act;           // first slot of its columns in the next level's active list
+    double lnb, rnb;   // neighbour bounds outside the cluster (parent coordinates)
+};
+
+struct SingleItem {
+    int col;
+    int node;
+};
+
+struct LevelCounters {
+    int nsingle;
+    int ncluster;
+    int maxcluster;
+    int nactive;         // columns in clusters (refined on the next level)
+    long long pool_need; // doubles needed for the child representations
+};
+
+struct DevInfo {
+    unsigned long long sturm_steps;
+    unsigned long long shift_steps;
+    unsigned long long twisted_steps;
+    unsigned long long rqi_iters;
+    int rqi_max;
+    int fallbacks;
+    int new_rrr;
+    int untested;
+    int nclusters;
+    int largest;
+    int dmax;
+    int status[8];
+};
+
+// ------------------------------------------------------------------ bit helpers
+
+__device__ __forceinline__ int sign_bit(double x) {
+    return (int)((unsigned long long)__double_as_longlong(x) >> 63);
+}
+__device__ __forceinline__ int biased_exp(double x) {
+    return (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+}
+// 2^k for -1022 <= k <= 1023 (exact power of two built from the exponent field).
+__device__ __forceinline__ double pow2i(int k) {
+    return __longlong_as_double((long long)(k + 1023) << 52);
+}
+__device__ __forceinline__ bool is_zero(double x) {
+    return (((unsigned long long)__double_as_longlong(x)) << 1) == 0ull;
+}
+__device__ __forceinline__ bool is_finite(double x) {
+    return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
+}
+
+// Counter-based SplitMix64 (Steele, Lea, Flood 2014): output for counter i of stream
+// seed, mapped to a uniform double in (-1, 1).  Draws the random relative perturbation
+// of the root representation (Alg. MRRR line 2).
+__device__ __forceinline__ double splitmix_pm1(unsigned long long seed, unsigned long long i) {
+    unsigned long long z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    return 2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+}
+
+// ------------------------------------------------------------------ Sturm counts
+//
+// NegCount on L D L^T (App. B, Alg. NegCount on LDL^T) counts the negative pivots d+_i
+// of L+ D+ L+^T = L D L^T - sigma I, computed by the dstqds recurrence
+//     d+_i = d_i + s_i,   s_{i+1} = (s_i / d+_i) dll_i - sigma,   s_1 = -sigma.
+// On GB300 an FP64 division costs ~10 FMA slots of throughput and ~650 cycles of
+// latency, so the recurrence is evaluated in homogeneous (division-free) form: with
+// c_i = d+_1 ... d+_i (times a positive power-of-two scale) and a_i = s_i c_{i-1},
+//     c_i = d_i c_{i-1} + a_i,    a_{i+1} = dll_i a_i - sigma c_i,
+// and sign(d+_i) = sign(c_i) xor sign(c_{i-1}).  Each rounding error can be pushed onto
+// d_i or dll_i as an O(eps) relative perturbation (the pair (a, c) only shares a
+// positive scale), so the count is exact for a relatively perturbed representation,
+// the property bisection on an RRR relies on.  (a, c) are rescaled by a power of two
+// when c leaves [2^-200, 2^200].  A pivot that is exactly zero is replaced by a tiny
+// negative one (SignBit(-0) = 1, App. B remarks).  Critical path: two dependent FMAs
+// per step.
+__device__ __forceinline__ int negcount_ldl(int n, const double *__restrict__ d,
+                                            const double *__restrict__ dll, double sigma) {
+    double a = -sigma, cp = 1.0;
+    int sp = 0, cnt = 0;
+    for (int i = 0; i < n - 1; ++i) {
+        const double t = __ldg(dll + i) * a;
+        double c = fma(__ldg(d + i), cp, a);
+        if (is_zero(c)) c = -cp * 0x1p-80;
+        const int sc = sign_bit(c);
+        cnt += sc ^ sp;
+        a = fma(-sigma, c, t);
+        const int ex = biased_exp(c);
+        if ((unsigned)(ex - (1023 - 200)) > 400u) {
+            const double s = pow2i(1023 - ex);
+            c *= s;
+            a *= s;
+        }
+        cp = c;
+        sp = sc;
+    }
+    double c = fma(__ldg(d + n - 1), cp, a);
+    int sc = is_zero(c) ? (sp ^ 1) : sign_bit(c);
+    cnt += sc ^ sp;
+    return cnt;
+}
+
+// Same count at two shifts at once (independent chains interleaved for latency
+// hiding); returns both counts.
+__device__ __forceinline__ void negcount_ldl2(int n, const double *__restrict__ d,
+                                              const double *__restrict__ dll, double s0,
+                                              double s1, int &k0, int &k1) {
+    double a0 = -s0, c0 = 1.0, a1 = -s1, c1 = 1.0;
+    int p0 = 0, p1 = 0, n0 = 0, n1 = 0;
+    for (int i = 0; i < n - 1; ++i) {
+        const double di = __ldg(d + i), li = __ldg(dll + i);
+        const double t0 = li * a0, t1 = li * a1;
+        double x0 = fma(di, c0, a0), x1 = fma(di, c1, a1);
+        if (is_zero(x0)) x0 = -c0 * 0x1p-80;
+        if (is_zero(x1)) x1 = -c1 * 0x1p-80;
+        const int q0 = sign_bit(x0), q1 = sign_bit(x1);
+        n0 += q0 ^ p0;
+        n1 += q1 ^ p1;
+        a0 = fma(-s0, x0, t0);
+        a1 = fma(-s1, x1, t1);
+        const int e0 = biased_exp(x0), e1 = biased_exp(x1);
+        if ((unsigned)(e0 - (1023 - 200)) > 400u) { const double s = pow2i(1023 - e0); x0 *= s; a0 *= s; }
+        if ((unsigned)(e1 - (1023 - 200)) > 400u) { const double s = pow2i(1023 - e1); x1 *= s; a1 *= s; }
+        c0 = x0; c1 = x1; p0 = q0; p1 = q1;
+    }
+    double x0 = fma(__ldg(d + n - 1), c0, a0), x1 = fma(__ldg(d + n - 1), c1, a1);
+    n0 += (is_zero(x0) ? (p0 ^ 1) : sign_bit(x0)) ^ p0;
+    n1 += (is_zero(x1) ? (p1 ^ 1) : sign_bit(x1)) ^ p1;
+    k0 = n0;
+    k1 = n1;
+}
+
+// NegCount on T itself (App. B, Alg. NegCount on T) in single precision, used only to
+// locate the extremal eigenvalues roughly before the root shift is chosen (the FP64
+// factorization then verifies definiteness).  Homogeneous three-term form of the pivot
+// recurrence d_i = (alpha_i - sigma) - beta_{i-1}^2 / d_{i-1}:
+//     p_i = (alpha_i - sigma) p_{i-1} - beta_{i-1}^2 p_{i-2},   d_i = p_i / p_{i-1}.
+__device__ __forceinline__ int negcount_T_f32(int n, const float *__restrict__ af,
+                                              const float *__restrict__ b2f, float sigma) {
+    float pm2 = 0.f, pm1 = 1.f;
+    int sp = 0, cnt = 0;
+    for (int i = 0; i < n; ++i) {
+        const float q = (i > 0) ? b2f[i - 1] * pm2 : 0.f;
+        float p = fmaf(af[i] - sigma, pm1, -q);
+        if (p == 0.f) p = -pm1 * 0x1p-30f;
+        const int sc = __float_as_int(p) < 0 ? 1 : 0;
+        cnt += sc ^ sp;
+        const int ex = (__float_as_int(p) >> 23) & 0xff;
+        if ((unsigned)(ex - (127 - 40)) > 80u) {
+            const float s = __int_as_float((254 - ex) << 23); // 2^(127-ex)
+            p *= s;
+            pm1 *= s;
+        }
+        pm2 = pm1;
+        pm1 = p;
+        sp = sc;
+    }
+    return cnt;
+}
+
+} // namespace mr3

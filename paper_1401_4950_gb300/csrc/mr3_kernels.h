@@ -1,0 +1,75 @@
+// mr3_kernels.h -- host-side launchers of the MRRR kernels (one per .cu stage).
+#pragma once
+#include <cuda_runtime.h>
+#include "mr3.h"
+#include "mr3_internal.cuh"
+
+namespace mr3 {
+
+// ---- prologue (mr3_prologue.cu)
+// Per matrix: Gershgorin norm of the whole matrix; flags rows that start a block.
+void launch_mat_norm(int nmat, MatDesc *mats, const double *d, const double *e, int *bad_input,
+                     cudaStream_t s);
+void launch_split_flags(int nmat, const MatDesc *mats, long long nrows, const double *d,
+                        const double *e, int *flags, cudaStream_t s);
+// Exclusive scan of n ints (in place allowed); *total (device) gets the sum.
+void launch_exclusive_scan(const int *in, int *out, long long n, int *total, int *tmp,
+                           cudaStream_t s);
+size_t scan_tmp_ints(long long n);
+// Build block descriptors from the scanned flags.
+void build_blocks(long long nrows, const int *flags, const int *scanned, const int *nblk_dev,
+                  int nblk_host, int nmat, MatDesc *mats, BlkDesc *blks, cudaStream_t s);
+// Per block: Gershgorin, selected local index range, output columns (range != ALL
+// needs the per-matrix index/value data in mats).
+void launch_blk_setup(int nblk, BlkDesc *blks, int nmat, MatDesc *mats, const double *d,
+                      const double *e, int range, cudaStream_t s);
+// Range INDEX on matrices that split into several blocks: per-block index ranges.
+void launch_index_multi(int nmat, MatDesc *mats, BlkDesc *blks, const double *d,
+                        const double *e, cudaStream_t s);
+// Per matrix: columns of each block and m.
+void launch_assign_columns(int nmat, MatDesc *mats, BlkDesc *blks, int range, cudaStream_t s);
+// Root representation of every block (Alg. MRRR lines 1-2).
+void launch_root(int nblk, BlkDesc *blks, const double *d, const double *e, double *pool0,
+                 float *f32scratch, unsigned long long seed, cudaStream_t s);
+// Level-0 nodes, per-column state and starting intervals.
+void launch_init_columns(int nblk, const BlkDesc *blks, Node *nodes, int *cnode, int *jloc,
+                         double *lo, double *hi, int mtotal, cudaStream_t s);
+// Gaps to the eigenvalues just outside a subset (range != ALL).
+void launch_outer_gaps(int nblk, const BlkDesc *blks, Node *nodes, const double *pool0,
+                       double rtol, DevInfo *info, cudaStream_t s);
+void launch_zero_z(int nmat, const MatDesc *mats, double *Z, cudaStream_t s);
+
+// ---- representation tree (mr3_levels.cu)
+// Multisection with L lanes (1, 2, 4, ..., 32) per eigenvalue over ngroups columns
+// (list[g], or g itself when list is NULL).
+void launch_bisect(int ngroups, const int *list, int L, int mtotal, const int *cnode,
+                   const Node *nodes, const BlkDesc *blks, const double *pool, const int *jloc,
+                   double *lo, double *hi, double rtol, const double *tau_of_node, DevInfo *info,
+                   cudaStream_t s);
+// Shared grid of Sturm counts giving the starting intervals of the root level.
+void launch_grid(int nblk, const BlkDesc *blks, const Node *nodes, const double *pool, int *grid,
+                 double *lo, double *hi, int max_m, DevInfo *info, cudaStream_t s);
+void launch_classify(int nnode, const Node *nodes, const BlkDesc *blks, const double *lo,
+                     const double *hi, double gaptol, double *gapl, double *gapr,
+                     SingleItem *singles, ClusterItem *clusters, long long *cluster_rep,
+                     int *cnode, LevelCounters *ctr, DevInfo *info, cudaStream_t s);
+void launch_shift(int ncluster, const ClusterItem *clusters, const long long *cluster_rep,
+                  const Node *nodes, const BlkDesc *blks, const double *pool, double *childpool,
+                  Node *child_nodes, double *child_tau, int *cnode, int *active_list,
+                  const int *jloc, double *lo, double *hi, int max_tries, unsigned fault_mask,
+                  DevInfo *info, cudaStream_t s);
+// Ascending eigenvalues: running-maximum fix for single-block matrices, flags for the rest.
+void launch_order_flags(int nmat, const MatDesc *mats, double *w, int *flags, cudaStream_t s);
+// Sort the m eigenpairs of matrix mi (temporaries: m values, n x m entries, m ints).
+void launch_sort_outputs(int mi, int m, const MatDesc *mats, double *w, double *Z, double *wtmp,
+                         double *ztmp, int *perm, cudaStream_t s);
+
+// ---- singletons (mr3_rqi.cu)
+void launch_rqi(int nsingle, const SingleItem *singles, const Node *nodes, const BlkDesc *blks,
+                const MatDesc *mats, const double *pool, const int *jloc, const double *lo,
+                const double *hi, const double *gapl, const double *gapr, const double *d,
+                const double *e, double *w, double *Z, double *scratch, int nslots, int nmax,
+                int max_rqi, unsigned fault_mask, int *work_counter, DevInfo *info,
+                cudaStream_t s);
+
+} // namespace mr3

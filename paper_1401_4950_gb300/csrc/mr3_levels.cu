@@ -1,0 +1,737 @@
+// mr3_levels.cu -- traversal of the representation tree, one level per launch group
+// (Alg. MRRR, breadth first): bisection to classification accuracy (Alg. Bisection),
+// classification by relative gaps (Sec. 3.2.3), and for every cluster a new
+// representation by a shift of the spectrum (Alg. "Shifting the spectrum", C-task).
+#include <float.h>
+#include <algorithm>
+#include "mr3_kernels.h"
+#include "mr3_df.cuh"
+
+namespace mr3 {
+
+#define FULL_MASK 0xffffffffu
+
+// ------------------------------------------------------------------ bisection
+
+// Sturm count at x for one node: double-float when the node's copy is exact enough and x
+// is representable (Ch. 5 x-bit eigenvalue approximation), else binary64.
+__device__ __forceinline__ int node_count(const Node &N, int n, const double *__restrict__ rep,
+                                          double x) {
+    if (N.dfok && df_safe(x)) {
+        const int k = negcount_df(n, (const float4 *)(rep + rep_df_offset(n)), df_from(x));
+        if (k >= 0) return k;
+    }
+    return negcount_ldl(n, rep, rep + 2 * n, x);
+}
+
+// Multisection (Alg. Bisection generalised to L interior points per sweep): a group of L
+// lanes owns one eigenvalue j of a node; each sweep the lanes count at the L interior
+// points of [lo, hi] (L + 1 equal parts) and a ballot of "count < j" picks the part that
+// holds lambda_j, so a sweep gains log2(L + 1) bits.  Stop when
+// hi - lo <= max(rtol max(|lo|, |hi|), atol).
+//
+// Refinement on a child (tau_of_node != NULL): the parent interval is mapped to the child
+// by subtracting tau and widened by 8 eps (|bound| + |tau|); the two ends are verified by
+// Sturm counts on the child; if they do not bracket lambda_j the interval is widened by the
+// paper's factor nu = 10 k_rr n eps, k_rr = 10 ((lambda (1 -+ nu) - tau)(1 -+ nu), end of
+// Sec. 3.2.3), then by powers of 2^8.
+//
+// Counts in double-float are exact for a relative perturbation of the representation of
+// a few units of 2^-47, so the final interval is widened by 32 n 2^-47 relative.
+__global__ void k_bisect2(int ngroups, const int *__restrict__ list, int L, int mtotal,
+                          const int *__restrict__ cnode, const Node *__restrict__ nodes,
+                          const BlkDesc *__restrict__ blks, const double *__restrict__ pool,
+                          const int *__restrict__ jloc, double *lo, double *hi, double rtol,
+                          const double *__restrict__ tau_of_node, DevInfo *info) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int gid = tid / L;
+    const int k = lane % L;
+    const int gbase = lane - k;
+    const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << gbase);
+    bool active = gid < ngroups;
+    int c = 0;
+    if (active) {
+        c = list ? list[gid] : gid;
+        active = c < mtotal && cnode[c] >= 0;
+    }
+    Node N;
+    int n = 1, j = 1;
+    const double *rep = pool;
+    double l = 0.0, h = 0.0;
+    unsigned long long steps = 0;
+    if (active) {
+        N = nodes[cnode[c]];
+        n = blks[N.blk].n;
+        rep = pool + N.rep;
+        j = jloc[c];
+        l = lo[c];
+        h = hi[c];
+    } else {
+        N.dfok = 0;
+    }
+    if (tau_of_node) {
+        // ---- map the parent interval to the child and verify it brackets lambda_j
+        double tau = 0.0, pl = l, ph = h;
+        if (active) {
+            tau = tau_of_node[cnode[c]];
+            const double m0 = 8.0 * kEps * (fmax(fabs(pl), fabs(ph)) + fabs(tau));
+            l = (pl - tau) - m0;
+            h = (ph - tau) + m0;
+        }
+        for (int attempt = 0; attempt < 8; ++attempt) {
+            int okL = 1, okH = 1;
+            if (active) {
+                if (L >= 2) {
+                    int cnt = 0;
+                    if (k < 2) { cnt = node_count(N, n, rep, k == 0 ? l : h); steps += n; }
+                    const int c0 = __shfl_sync(gmask, cnt, gbase), c1 = __shfl_sync(gmask, cnt, gbase + 1);
+                    okL = c0 < j;
+                    okH = c1 >= j;
+                } else {
+                    okL = node_count(N, n, rep, l) < j;
+                    okH = node_count(N, n, rep, h) >= j;
+                    steps += 2ull * n;
+                }
+            } else if (L >= 2) {
+                (void)__shfl_sync(gmask, 0, gbase);
+                (void)__shfl_sync(gmask, 0, gbase + 1);
+            }
+            const bool ok = okL && okH;
+            if (__all_sync(0xffffffffu, ok || !active)) break;
+            if (active && !ok) {
+                if (attempt == 0) {
+                    const double nu = 100.0 * n * kEps;
+                    double a = pl - nu * fabs(pl) - tau;
+                    a -= nu * fabs(a);
+                    double b = ph + nu * fabs(ph) - tau;
+                    b += nu * fabs(b);
+                    if (!okL) l = fmin(l, a);
+                    if (!okH) h = fmax(h, b);
+                } else {
+                    const double g = ldexp(fmax(h - l, 4.0 * kSafmin), 8);
+                    if (!okL) l -= g;
+                    if (!okH) h += g;
+                }
+            }
+        }
+    }
+    // ---- multisection
+    const double atol = 4.0 * kSafmin;
+    bool used_df = false;
+    for (int sweep = 0; sweep < 400; ++sweep) {
+        const double w = h - l;
+        bool done = !active || !(w > fmax(rtol * fmax(fabs(l), fabs(h)), atol));
+        const double x = l + (k + 1) * (w / (L + 1));
+        // no representable interior point left: the group stops
+        if (__ballot_sync(0xffffffffu, !(x > l && x < h)) & gmask) done = true;
+        if (__all_sync(0xffffffffu, done)) break;
+        int cnt = 0;
+        if (!done) {
+            used_df |= (N.dfok && df_safe(x));
+            cnt = node_count(N, n, rep, x);
+            steps += n;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, cnt < j);
+        const int t = __popc(bal & gmask);
+        const double xl = __shfl_sync(0xffffffffu, x, gbase + (t > 0 ? t - 1 : 0));
+        const double xh = __shfl_sync(0xffffffffu, x, gbase + (t < L ? t : L - 1));
+        if (!done) {
+            if (t > 0) l = xl;
+            if (t < L) h = xh;
+        }
+    }
+    const bool grp_df = (__ballot_sync(0xffffffffu, used_df) & gmask) != 0;
+    if (active && k == 0) {
+        if (grp_df) {
+            const double kap = 32.0 * n * 0x1p-47;
+            l -= kap * fabs(l);
+            h += kap * fabs(h);
+        }
+        lo[c] = l;
+        hi[c] = h;
+    }
+    for (int o = 16; o > 0; o >>= 1) steps += __shfl_xor_sync(0xffffffffu, steps, o);
+    if (lane == 0 && steps) atomicAdd(&info->sturm_steps, steps);
+}
+
+void launch_bisect(int ngroups, const int *list, int L, int mtotal, const int *cnode,
+                   const Node *nodes, const BlkDesc *blks, const double *pool, const int *jloc,
+                   double *lo, double *hi, double rtol, const double *tau_of_node, DevInfo *info,
+                   cudaStream_t s) {
+    if (ngroups <= 0) return;
+    const long long threads = (long long)ngroups * L;
+    const int bs = 128;
+    k_bisect2<<<(unsigned)((threads + bs - 1) / bs), bs, 0, s>>>(ngroups, list, L, mtotal, cnode,
+                                                                 nodes, blks, pool, jloc, lo, hi,
+                                                                 rtol, tau_of_node, info);
+}
+
+// Root level, most of a block's spectrum requested: G + 1 equally spaced points over the
+// block's shifted Gershgorin interval are counted once (one thread each) and every
+// requested eigenvalue takes the grid cell that holds it as its starting interval, so the
+// first log2(G) bits are shared by all eigenvalues instead of bisected one by one.
+__global__ void k_grid_counts(int nblk, const BlkDesc *__restrict__ blks, const Node *__restrict__ nodes,
+                              const double *__restrict__ pool, int *grid, DevInfo *info) {
+    const int b = blockIdx.y;
+    const BlkDesc B = blks[b];
+    const int m = B.j1 >= B.j0 ? B.j1 - B.j0 + 1 : 0;
+    const bool use = m > 0 && 4 * m >= B.n;
+    const int G = ((max(m, 32) + 31) / 32) * 32;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long steps = 0;
+    if (use && p <= G) {
+        int *cnt = grid + B.col0 + 64 * b;
+        if (p == 0) {
+            cnt[0] = 0;
+        } else if (p == G) {
+            cnt[G] = B.n;
+        } else {
+            const Node N = nodes[b];
+            const double a = B.gl - B.mu, z = B.gu - B.mu;
+            const double pad = 64.0 * (B.n + 1) * kEps * fmax(fabs(a), fabs(z)) + 4.0 * kSafmin;
+            const double ga = a - pad, gz = z + pad;
+            const double x = ga + (gz - ga) * ((double)p / G);
+            cnt[p] = node_count(N, B.n, pool + N.rep, x);
+            steps = B.n;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) steps += __shfl_xor_sync(0xffffffffu, steps, o);
+    if ((threadIdx.x & 31) == 0 && steps) atomicAdd(&info->sturm_steps, steps);
+}
+
+__global__ void k_grid_bracket(int nblk, const BlkDesc *__restrict__ blks, const int *__restrict__ grid,
+                               double *lo, double *hi) {
+    const int b = blockIdx.y;
+    if (b >= nblk) return;
+    const BlkDesc B = blks[b];
+    const int m = B.j1 >= B.j0 ? B.j1 - B.j0 + 1 : 0;
+    if (m == 0 || 4 * m < B.n) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m) return;
+    const int G = ((max(m, 32) + 31) / 32) * 32;
+    const int *cnt = grid + B.col0 + 64 * b;
+    const int j = B.j0 + t;
+    // largest p with cnt[p] < j (cnt[0] = 0 < j, cnt[G] = n >= j)
+    int a = 0, z = G;
+    while (z - a > 1) {
+        const int mid = (a + z) >> 1;
+        if (cnt[mid] < j) a = mid; else z = mid;
+    }
+    const double ga0 = B.gl - B.mu, gz0 = B.gu - B.mu;
+    const double pad = 64.0 * (B.n + 1) * kEps * fmax(fabs(ga0), fabs(gz0)) + 4.0 * kSafmin;
+    const double ga = ga0 - pad, gz = gz0 + pad;
+    const int c = B.col0 + t;
+    lo[c] = (a == 0) ? ga : ga + (gz - ga) * ((double)a / G);
+    hi[c] = (z == G) ? gz : ga + (gz - ga) * ((double)z / G);
+}
+
+void launch_grid(int nblk, const BlkDesc *blks, const Node *nodes, const double *pool, int *grid,
+                 double *lo, double *hi, int max_m, DevInfo *info, cudaStream_t s) {
+    if (nblk <= 0 || max_m <= 0) return;
+    const int G = ((std::max(max_m, 32) + 31) / 32) * 32;
+    dim3 g1((G + 1 + 63) / 64, nblk);
+    k_grid_counts<<<g1, 64, 0, s>>>(nblk, blks, nodes, pool, grid, info);
+    dim3 g2((max_m + 127) / 128, nblk);
+    k_grid_bracket<<<g2, 128, 0, s>>>(nblk, blks, grid, lo, hi);
+}
+
+// ------------------------------------------------------------------ classification
+
+// One warp per node.  Consecutive eigenvalues j, j+1 of the node are separated when
+//   reldist(j, j+1) = (lo_{j+1} - hi_j) / max(|lo_j|, |hi_j|, |lo_{j+1}|, |hi_{j+1}|) >= gaptol
+// (Sec. 3.2.3, Classification).  The boundary flags of 32 columns at a time are combined
+// with a ballot; groups of one column become singletons, longer groups clusters.  Items
+// are appended with one atomic per warp and kind.  gapl/gapr receive the absolute gaps
+// of every column to its neighbours (used by the RQI acceptance test).
+__global__ void k_classify(int nnode, const Node *__restrict__ nodes, const BlkDesc *__restrict__ blks,
+                           const double *__restrict__ lo, const double *__restrict__ hi,
+                           double gaptol, double *gapl, double *gapr, SingleItem *singles,
+                           ClusterItem *clusters, long long *cluster_rep, int *cnode,
+                           LevelCounters *ctr, DevInfo *info) {
+    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (w >= nnode) return;
+    const Node N = nodes[w];
+    if (N.c1 < N.c0) return;
+    const int nb = blks[N.blk].n;
+    int gstart = N.c0;
+    int maxsize = 0, nclus = 0;
+    for (int base = N.c0; base <= N.c1; base += 32) {
+        const int c = base + lane;
+        const bool valid = c <= N.c1;
+        double l = 0.0, h = 0.0, ln = 0.0, hn = 0.0;
+        bool end = false;
+        if (valid) {
+            l = lo[c];
+            h = hi[c];
+            if (c < N.c1) {
+                ln = lo[c + 1];
+                hn = hi[c + 1];
+                const double den = fmax(fmax(fabs(l), fabs(h)), fmax(fabs(ln), fabs(hn)));
+                const double rd = (ln - h) / den;
+                end = !(rd < gaptol); // also separates on NaN (never join on bad data)
+            } else {
+                end = true;
+            }
+            const double left = (c > N.c0) ? hi[c - 1] : N.lnb;
+            const double right = (c < N.c1) ? ln : N.rnb;
+            gapl[c] = l - left;
+            gapr[c] = right - h;
+            cnode[c] = -1;
+        }
+        const unsigned mask = __ballot_sync(FULL_MASK, end);
+        int gs = gstart;
+        if (end) {
+            const unsigned prev = mask & ((1u << lane) - 1u);
+            if (prev) gs = base + (31 - __clz(prev)) + 1;
+        }
+        const int size = end ? c - gs + 1 : 0;
+        const bool single = end && size == 1;
+        const bool clus = end && size >= 2;
+        const unsigned ms = __ballot_sync(FULL_MASK, single);
+        const unsigned mc = __ballot_sync(FULL_MASK, clus);
+        int sbase = 0, cbase = 0;
+        long long pbase = 0;
+        if (lane == 0) {
+            if (ms) sbase = atomicAdd(&ctr->nsingle, __popc(ms));
+            if (mc) {
+                cbase = atomicAdd(&ctr->ncluster, __popc(mc));
+                pbase = atomicAdd((unsigned long long *)&ctr->pool_need,
+                                  (unsigned long long)((long long)kRepStride * nb * __popc(mc)));
+            }
+        }
+        sbase = __shfl_sync(FULL_MASK, sbase, 0);
+        cbase = __shfl_sync(FULL_MASK, cbase, 0);
+        pbase = __shfl_sync(FULL_MASK, pbase, 0);
+        // reserve next-level active-list slots for the cluster columns (warp prefix sum)
+        int csz = clus ? size : 0, incl = csz;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL_MASK, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int ctot = __shfl_sync(FULL_MASK, incl, 31);
+        int abase = 0;
+        if (lane == 0 && ctot) abase = atomicAdd(&ctr->nactive, ctot);
+        abase = __shfl_sync(FULL_MASK, abase, 0);
+        const unsigned below = (1u << lane) - 1u;
+        if (single) {
+            SingleItem it;
+            it.col = c;
+            it.node = w;
+            singles[sbase + __popc(ms & below)] = it;
+        }
+        if (clus) {
+            const int k = __popc(mc & below);
+            ClusterItem it;
+            it.node = w;
+            it.c0 = gs;
+            it.c1 = c;
+            it.act = abase + incl - csz;
+            it.lnb = (gs > N.c0) ? hi[gs - 1] : N.lnb;
+            it.rnb = (c < N.c1) ? ln : N.rnb;
+            clusters[cbase + k] = it;
+            cluster_rep[cbase + k] = pbase + (long long)kRepStride * nb * k;
+            maxsize = max(maxsize, size);
+            nclus++;
+        }
+        if (mask) gstart = base + (31 - __clz(mask)) + 1;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        maxsize = max(maxsize, __shfl_xor_sync(FULL_MASK, maxsize, o));
+        nclus += __shfl_xor_sync(FULL_MASK, nclus, o);
+    }
+    if (lane == 0 && nclus) {
+        atomicMax(&ctr->maxcluster, maxsize);
+        atomicMax(&info->largest, maxsize);
+        atomicAdd(&info->nclusters, nclus);
+        atomicMax(&info->dmax, N.depth + 1);
+    }
+}
+
+void launch_classify(int nnode, const Node *nodes, const BlkDesc *blks, const double *lo,
+                     const double *hi, double gaptol, double *gapl, double *gapr,
+                     SingleItem *singles, ClusterItem *clusters, long long *cluster_rep,
+                     int *cnode, LevelCounters *ctr, DevInfo *info, cudaStream_t s) {
+    if (nnode <= 0) return;
+    const int wpb = 4;
+    k_classify<<<(nnode + wpb - 1) / wpb, 32 * wpb, 0, s>>>(nnode, nodes, blks, lo, hi, gaptol,
+                                                            gapl, gapr, singles, clusters,
+                                                            cluster_rep, cnode, ctr, info);
+}
+
+// ------------------------------------------------------------------ cluster shift
+
+// Trial dstqds L+ D+ L+^T = L D L^T - tau I in homogeneous form (see negcount_ldl).
+// Existence: no exact zero pivot and finite values.  Element growth: max |d+_i|, the
+// division c_i / c_{i-1} being off the recurrence's critical path.  With store, the
+// unscaled c_i go to U[i] and the power-of-two rescale applied after step i to K[i].
+__device__ void trial_shift(int n, const double *__restrict__ d, const double *__restrict__ dll,
+                            double tau, bool store, double *U, int *K, int kstride, bool &exists,
+                            double &growth) {
+    double a = -tau, cp = 1.0;
+    bool ok = is_finite(tau);
+    double g = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double c = fma(__ldg(d + i), cp, a);
+        if (is_zero(c)) { ok = false; c = -cp * 0x1p-80; }
+        const double dp = c / cp;
+        g = fmax(g, fabs(dp));
+        if (!is_finite(c)) ok = false;
+        int k = 0;
+        if (i < n - 1) {
+            const double t = __ldg(dll + i) * a;
+            a = fma(-tau, c, t);
+            const int ex = biased_exp(c);
+            if ((unsigned)(ex - (1023 - 200)) > 400u) {
+                k = 1023 - ex;
+                const double s = pow2i(k);
+                if (store) U[i] = c;
+                c *= s;
+                a *= s;
+            } else if (store) {
+                U[i] = c;
+            }
+        } else if (store) {
+            U[i] = c;
+        }
+        if (store) K[(size_t)i * kstride] = k;
+        cp = c;
+    }
+    exists = ok && is_finite(g);
+    growth = exists ? g : INFINITY;
+}
+
+// One warp per cluster {p..q} of node P (Alg. "Shifting the spectrum" inside a C-task).
+//  1. Refine the cluster's extreme eigenvalues (lanes 0-15: lambda_p, lanes 16-31:
+//     lambda_q) by 16-point multisection until the interval is below 1e-3 of a lower
+//     bound of the gap to the inner neighbour, or at full accuracy (4 eps |lambda|).
+//  2. Candidates tau_l = lo_p - 100 eps |lo_p| and tau_r = hi_q + 100 eps |hi_q| (lanes 0, 1);
+//     a candidate exists when its factorization has no zero pivot and stays finite; of
+//     existing ones the smaller growth max|d+_i| is taken; it is accepted when
+//     max|d+_i| <= 8 spdiam(M_root).  Otherwise back off:
+//     tau_l - 2^(t-1) delta, tau_r + 2^(t-1) delta, delta = max(100 eps |lambda|, 1e-3 W)
+//     (W the cluster width), t = 1 .. max_tries-1, evaluated in parallel; the first t
+//     with an accepted candidate wins, else the least growth overall (counted untested).
+//  3. The winner's c_i give the child: d+_i = c_i / c_{i-1}, l+_i = dl_i / d+_i,
+//     dl+_i = d+_i l+_i, dll+_i = dl+_i l+_i, converted in place by chunks of 32.
+__global__ void k_shift(int ncluster, const ClusterItem *__restrict__ clusters,
+                        const long long *__restrict__ cluster_rep, const Node *__restrict__ nodes,
+                        const BlkDesc *__restrict__ blks, const double *__restrict__ pool,
+                        double *childpool, Node *child_nodes, double *child_tau, int *cnode,
+                        int *active_list, const int *__restrict__ jloc, double *lo, double *hi,
+                        int max_tries, unsigned fault_mask, DevInfo *info) {
+    const int ci = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (ci >= ncluster) return;
+    const ClusterItem C = clusters[ci];
+    const Node P = nodes[C.node];
+    const BlkDesc B = blks[P.blk];
+    const int n = B.n;
+    const double *pd = pool + P.rep, *pdl = pd + n, *pdll = pd + 2 * n;
+    double *cd = childpool + cluster_rep[ci], *cdl = cd + n, *cdll = cd + 2 * n;
+    const int p = C.c0, q = C.c1;
+    unsigned long long steps = 0;
+
+    // ---- 1. refine the cluster ends
+    const int half = lane >> 4, k = lane & 15;
+    const int tgt = half ? jloc[q] : jloc[p];
+    double L = half ? lo[q] : lo[p];
+    double H = half ? hi[q] : hi[p];
+    double nb = half ? hi[q - 1] : lo[p + 1]; // bound on the inner neighbour
+    for (int sweep = 0; sweep < 16; ++sweep) {
+        const double w = H - L;
+        const double gap_lb = half ? (L - nb) : (nb - H);
+        const double tol = fmax(4.0 * kEps * fmax(fabs(L), fabs(H)), 1e-3 * fmax(gap_lb, 0.0));
+        const bool done = !(w > tol);
+        const unsigned dm = __ballot_sync(FULL_MASK, done);
+        if ((dm & 0x00010001u) == 0x00010001u) break;
+        const double x = L + (k + 1) * (w / 17.0);
+        int cnt = 0;
+        if (!done) {
+            cnt = (w > 1e-11 * fmax(fabs(L), fabs(H))) ? node_count(P, n, pd, x)
+                                                        : negcount_ldl(n, pd, pdll, x);
+            steps += n;
+        }
+        const unsigned bal = __ballot_sync(FULL_MASK, cnt < tgt);
+        const int t = __popc((bal >> (16 * half)) & 0xffffu);
+        const double xl = __shfl_sync(FULL_MASK, x, 16 * half + (t > 0 ? t - 1 : 0));
+        const double xh = __shfl_sync(FULL_MASK, x, 16 * half + (t < 16 ? t : 15));
+        // samples that bound the inner neighbour: left end, count <= j_p gives
+        // lambda_{p+1} >= x (take the largest); right end, count >= j_q - 1 gives
+        // lambda_{q-1} < x (take the smallest)
+        const bool nbl = half ? (cnt >= tgt - 1) : (cnt <= tgt);
+        const unsigned hb = (__ballot_sync(FULL_MASK, nbl) >> (16 * half)) & 0xffffu;
+        const int first = hb ? __ffs(hb) - 1 : 0, last = hb ? 31 - __clz(hb) : 0;
+        const double xf = __shfl_sync(FULL_MASK, x, 16 * half + first);
+        const double xlst = __shfl_sync(FULL_MASK, x, 16 * half + last);
+        if (!done) {
+            if (hb) nb = half ? fmin(nb, xf) : fmax(nb, xlst);
+            if (t > 0) L = xl;
+            if (t < 16) H = xh;
+        }
+    }
+    if (lane == 0) { lo[p] = L; hi[p] = H; }
+    if (lane == 16) { lo[q] = L; hi[q] = H; }
+    const double Lp = __shfl_sync(FULL_MASK, L, 0);
+    const double Hq = __shfl_sync(FULL_MASK, H, 16);
+
+    // ---- 2. shift candidates
+    const double tau_l0 = Lp - 100.0 * kEps * fabs(Lp);
+    const double tau_r0 = Hq + 100.0 * kEps * fabs(Hq);
+    const double W = Hq - Lp;
+    const double delta = fmax(100.0 * kEps * fmax(fabs(Lp), fabs(Hq)), 1e-3 * W);
+    const double thresh = 8.0 * B.spdiam;
+    const bool reject_all = (fault_mask & MR3_FAULT_SHIFT_REJECT) != 0;
+    int *K = (int *)cdll; // int2 per element: .x lane-0 candidate, .y lane-1 candidate
+    bool ex = false;
+    double g = INFINITY;
+    if (lane < 2) {
+        double tau = lane == 0 ? tau_l0 : tau_r0;
+        if (lane == 0 && (fault_mask & MR3_FAULT_NAN_SHIFT)) tau = NAN;
+        trial_shift(n, pd, pdll, tau, true, lane == 0 ? cd : cdl, K + lane, 2, ex, g);
+        steps += n;
+    }
+    const int e0 = __shfl_sync(FULL_MASK, (int)ex, 0), e1 = __shfl_sync(FULL_MASK, (int)ex, 1);
+    const double g0 = __shfl_sync(FULL_MASK, g, 0), g1 = __shfl_sync(FULL_MASK, g, 1);
+    int win = -1;     // 0/1: stored candidate of try 0; 2: recompute needed
+    double tau = 0.0; // the winner's shift
+    bool untested = false;
+    {
+        int sel = -1;
+        if (e0 && e1) sel = (g0 <= g1) ? 0 : 1;
+        else if (e0) sel = 0;
+        else if (e1) sel = 1;
+        if (sel >= 0 && !reject_all && (sel == 0 ? g0 : g1) <= thresh) {
+            win = sel;
+            tau = sel == 0 ? tau_l0 : tau_r0;
+        }
+    }
+    if (win < 0) {
+        // back-off ladder: lane 2(t-1)+side for t = 1..T-1
+        const int T = max(2, min(max_tries, 16));
+        const int t = (lane >> 1) + 1;
+        const int side = lane & 1;
+        bool ex2 = false;
+        double g2 = INFINITY, tau2 = NAN;
+        if (t < T) {
+            const double off = ldexp(delta, t - 1);
+            tau2 = side ? tau_r0 + off : tau_l0 - off;
+            trial_shift(n, pd, pdll, tau2, false, nullptr, nullptr, 0, ex2, g2);
+            steps += n;
+        }
+        const bool pass = ex2 && !reject_all && g2 <= thresh;
+        // first t whose better existing candidate passes
+        int best_t = -1;
+        for (int tt = 1; tt < T; ++tt) {
+            const int lL = 2 * (tt - 1), lR = lL + 1;
+            const int exL = __shfl_sync(FULL_MASK, (int)ex2, lL), exR = __shfl_sync(FULL_MASK, (int)ex2, lR);
+            const double gL = __shfl_sync(FULL_MASK, g2, lL), gR = __shfl_sync(FULL_MASK, g2, lR);
+            int s = -1;
+            if (exL && exR) s = (gL <= gR) ? lL : lR;
+            else if (exL) s = lL;
+            else if (exR) s = lR;
+            if (s >= 0 && __shfl_sync(FULL_MASK, (int)pass, s)) { best_t = s; break; }
+        }
+        if (best_t >= 0) {
+            tau = __shfl_sync(FULL_MASK, tau2, best_t);
+        } else {
+            // least element growth over every computed candidate (try 0 included)
+            double gb = g2;
+            int lb = lane;
+            for (int o = 16; o > 0; o >>= 1) {
+                const double og = __shfl_xor_sync(FULL_MASK, gb, o);
+                const int ol = __shfl_xor_sync(FULL_MASK, lb, o);
+                if (og < gb || (og == gb && ol < lb)) { gb = og; lb = ol; }
+            }
+            const double tb = __shfl_sync(FULL_MASK, tau2, lb);
+            if (e0 && g0 <= gb && (!e1 || g0 <= g1)) { win = 0; tau = tau_l0; }
+            else if (e1 && g1 <= gb) { win = 1; tau = tau_r0; }
+            else if (isfinite(gb)) { tau = tb; }
+            else { win = 0; tau = tau_l0; } // nothing exists: keep try 0 (flagged untested)
+            untested = true;
+        }
+        if (win < 0) {
+            win = 2;
+            bool dummy_e;
+            double dummy_g;
+            if (lane == 0) { trial_shift(n, pd, pdll, tau, true, cd, K, 2, dummy_e, dummy_g); steps += n; }
+        }
+    }
+    __syncwarp();
+
+    // ---- 3. convert the stored c_i into the child representation (in place), with its
+    // double-float copy for the bisection
+    const double *U = (win == 1) ? cdl : cd;
+    const int kofs = (win == 1) ? 1 : 0;
+    float4 *cdf = (float4 *)(cd + rep_df_offset(n));
+    double carry_u = 1.0;
+    int carry_k = 0;
+    bool dfok = true;
+    for (int base = 0; base < n; base += 32) {
+        const int i = base + lane;
+        const double ui = (i < n) ? U[i] : 1.0;
+        const int ki = (i < n) ? K[2 * i + kofs] : 0;
+        double up = __shfl_up_sync(FULL_MASK, ui, 1);
+        int kp = __shfl_up_sync(FULL_MASK, ki, 1);
+        if (lane == 0) { up = carry_u; kp = carry_k; }
+        carry_u = __shfl_sync(FULL_MASK, ui, 31);
+        carry_k = __shfl_sync(FULL_MASK, ki, 31);
+        __syncwarp();
+        if (i < n) {
+            const double dp = (ui / up) * pow2i(-kp);
+            double dllp = 0.0;
+            cd[i] = dp;
+            if (i < n - 1) {
+                const double lp = pdl[i] / dp;
+                const double dlp = dp * lp;
+                dllp = dlp * lp;
+                cdl[i] = dlp;
+                cdll[i] = dllp;
+            } else {
+                cdl[i] = 0.0;
+                cdll[i] = 0.0;
+            }
+            const dfloat a = df_from(dp), b = df_from(dllp);
+            cdf[i] = make_float4(a.h, a.l, b.h, b.l);
+            dfok &= df_safe(dp) && df_safe(dllp) && is_finite(dp) && is_finite(dllp);
+        }
+        __syncwarp();
+    }
+    dfok = __all_sync(FULL_MASK, dfok);
+
+    // ---- 4. child node
+    for (int c = p + lane; c <= q; c += 32) {
+        cnode[c] = ci;
+        active_list[C.act + (c - p)] = c;
+    }
+    if (lane == 0) {
+        Node Cn;
+        Cn.rep = cluster_rep[ci];
+        Cn.blk = P.blk;
+        Cn.c0 = p;
+        Cn.c1 = q;
+        Cn.depth = P.depth + 1;
+        Cn.dfok = dfok ? 1 : 0;
+        Cn.sigma = P.sigma + tau;
+        Cn.lnb = C.lnb - tau;
+        Cn.rnb = C.rnb - tau;
+        child_nodes[ci] = Cn;
+        child_tau[ci] = tau;
+        atomicAdd(&info->new_rrr, 1);
+        if (untested) { atomicAdd(&info->untested, 1); atomicAdd(&info->status[MR3_SUNTESTED_RRR], 1); }
+    }
+    for (int o = 16; o > 0; o >>= 1) steps += __shfl_xor_sync(FULL_MASK, steps, o);
+    if (lane == 0 && steps) atomicAdd(&info->shift_steps, steps);
+}
+
+void launch_shift(int ncluster, const ClusterItem *clusters, const long long *cluster_rep,
+                  const Node *nodes, const BlkDesc *blks, const double *pool, double *childpool,
+                  Node *child_nodes, double *child_tau, int *cnode, int *active_list,
+                  const int *jloc, double *lo, double *hi, int max_tries, unsigned fault_mask,
+                  DevInfo *info, cudaStream_t s) {
+    if (ncluster <= 0) return;
+    const int wpb = 2;
+    k_shift<<<(ncluster + wpb - 1) / wpb, 32 * wpb, 0, s>>>(ncluster, clusters, cluster_rep, nodes,
+                                                           blks, pool, childpool, child_nodes,
+                                                           child_tau, cnode, active_list, jloc, lo,
+                                                           hi, max_tries, fault_mask, info);
+}
+
+// ------------------------------------------------------------------ output order
+
+// Per matrix (one warp): eigenvalues of a single block come out in order up to rounding
+// (Rayleigh quotients of eigenvalues equal to working accuracy may differ by ulps in
+// either direction): make them ascending by a running maximum, which moves a value by at
+// most that rounding.  Matrices that split into several blocks come out block by block
+// and are flagged for a sort.
+__global__ void k_order_fix(int nmat, const MatDesc *__restrict__ mats, double *w, int *flags) {
+    const int mi = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (mi >= nmat) return;
+    const MatDesc M = mats[mi];
+    if (M.nblk > 1) {
+        int bad = 0;
+        for (int t = lane; t + 1 < M.m; t += 32) bad |= (w[M.woff + t] > w[M.woff + t + 1]);
+        bad = __any_sync(FULL_MASK, bad);
+        if (lane == 0) flags[mi] = bad;
+        return;
+    }
+    double carry = -INFINITY;
+    for (int base = 0; base < M.m; base += 32) {
+        const int t = base + lane;
+        double v = (t < M.m) ? w[M.woff + t] : -INFINITY;
+        for (int o = 1; o < 32; o <<= 1) {
+            const double y = __shfl_up_sync(FULL_MASK, v, o);
+            if (lane >= o) v = fmax(v, y);
+        }
+        v = fmax(v, carry);
+        if (t < M.m) w[M.woff + t] = v;
+        carry = __shfl_sync(FULL_MASK, v, 31);
+    }
+    if (lane == 0) flags[mi] = 0;
+}
+
+void launch_order_flags(int nmat, const MatDesc *mats, double *w, int *flags, cudaStream_t s) {
+    if (nmat > 0) k_order_fix<<<(nmat + 3) / 4, 128, 0, s>>>(nmat, mats, w, flags);
+}
+
+// Sort of one matrix's eigenpairs: the rank of each eigenvalue (ties by position) by one
+// thread per eigenvalue over the values staged in shared-memory tiles, then a gather of
+// the Z columns into a temporary and a copy back (one warp per column, coalesced).
+__global__ void k_rank(const MatDesc *__restrict__ mats, int mi, const double *__restrict__ w,
+                       int *perm, double *wtmp) {
+    __shared__ double tile[1024];
+    const MatDesc M = mats[mi];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const double x = (t < M.m) ? w[M.woff + t] : 0.0;
+    int r = 0;
+    for (int base = 0; base < M.m; base += 1024) {
+        __syncthreads();
+        for (int u = threadIdx.x; u < 1024; u += blockDim.x)
+            tile[u] = (base + u < M.m) ? w[M.woff + base + u] : INFINITY;
+        __syncthreads();
+        const int lim = min(1024, M.m - base);
+        for (int u = 0; u < lim; ++u) {
+            const double y = tile[u];
+            r += (y < x) || (y == x && base + u < t);
+        }
+    }
+    if (t < M.m) {
+        perm[t] = r;
+        wtmp[r] = x;
+    }
+}
+
+__global__ void k_gather_cols(const MatDesc *__restrict__ mats, int mi, const int *__restrict__ perm,
+                              const double *__restrict__ Z, double *ztmp) {
+    const MatDesc M = mats[mi];
+    const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (col >= M.m) return;
+    const double *src = Z + M.zoff + (long long)col * M.ldz;
+    double *dst = ztmp + (long long)perm[col] * M.n;
+    for (int i = lane; i < M.n; i += 32) dst[i] = src[i];
+}
+
+__global__ void k_copy_back(const MatDesc *__restrict__ mats, int mi, const double *__restrict__ wtmp,
+                            const double *__restrict__ ztmp, double *w, double *Z) {
+    const MatDesc M = mats[mi];
+    const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (col >= M.m) return;
+    if (lane == 0) w[M.woff + col] = wtmp[col];
+    const double *src = ztmp + (long long)col * M.n;
+    double *dst = Z + M.zoff + (long long)col * M.ldz;
+    for (int i = lane; i < M.n; i += 32) dst[i] = src[i];
+}
+
+void launch_sort_outputs(int mi, int m, const MatDesc *mats, double *w, double *Z, double *wtmp,
+                         double *ztmp, int *perm, cudaStream_t s) {
+    if (m <= 1) return;
+    k_rank<<<(m + 255) / 256, 256, 0, s>>>(mats, mi, w, perm, wtmp);
+    k_gather_cols<<<(m + 7) / 8, 256, 0, s>>>(mats, mi, perm, Z, ztmp);
+    k_copy_back<<<(m + 7) / 8, 256, 0, s>>>(mats, mi, wtmp, ztmp, w, Z);
+}
+
+} // namespace mr3

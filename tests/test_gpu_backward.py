@@ -1,0 +1,144 @@
+"""Backward pass (mr3_backward): closed forms, invariants, a dense-eigh autograd reference,
+and central finite differences of the loss sum(g . lambda) + sum(G o Z)."""
+import numpy as np
+import pytest
+
+import oracle
+import testmats as tm
+
+pytestmark = pytest.mark.gpu
+
+
+def _fwd(d, e):
+    import torch
+    import paper_1401_4950_gb300 as mr3
+    w, Z, _ = mr3.stemr(torch.tensor(d, device="cuda"), torch.tensor(e, device="cuda"))
+    return w, Z
+
+
+def _bwd(w, Z, g=None, G=None):
+    import torch
+    import paper_1401_4950_gb300 as mr3
+    gt = None if g is None else torch.tensor(g, device="cuda")
+    Gt = None if G is None else torch.tensor(G, device="cuda").t().contiguous().t()
+    dd, de = mr3.backward(w, Z, gt, Gt)
+    torch.cuda.synchronize()
+    return dd.cpu().numpy(), de.cpu().numpy()
+
+
+@pytest.mark.parametrize("n", [1, 2, 50, 1000])
+def test_eigenvalue_part_closed_forms(cuda, n):
+    d, e = tm.random_uniform(n, 11, 12)
+    w, Z = _fwd(d, e)
+    # sum lambda = trace T  =>  dbar = 1, ebar = 0
+    dd, de = _bwd(w, Z, g=np.ones(n))
+    assert np.max(np.abs(dd - 1.0)) <= 1e-12 and (n == 1 or np.max(np.abs(de)) <= 1e-12)
+    # sum lambda^2 / 2 = ||T||_F^2 / 2  =>  dbar = d, ebar = 2 e
+    dd, de = _bwd(w, Z, g=w.cpu().numpy())
+    assert np.max(np.abs(dd - d)) <= 1e-12
+    if n > 1:
+        assert np.max(np.abs(de - 2 * e)) <= 1e-12
+
+
+def test_vector_part_vanishes_for_G_equal_Z(cuda):
+    # dz_i is orthogonal to z_i for unit vectors, so G = Z contributes nothing
+    d, e = tm.random_uniform(300, 21, 22)
+    w, Z = _fwd(d, e)
+    dd, de = _bwd(w, Z, g=None, G=Z.cpu().numpy())
+    assert np.max(np.abs(dd)) <= 1e-9 and np.max(np.abs(de)) <= 1e-9
+
+
+def _loss_grad_dense(d, e, g, G):
+    """Reference gradient through torch.linalg.eigh (autograd) on the dense T, CPU FP64,
+    with the eigenvector signs of the CUDA solve."""
+    import torch
+    dt = torch.tensor(d, requires_grad=True)
+    et = torch.tensor(e, requires_grad=True)
+    T = torch.diag(dt) + torch.diag(et, 1) + torch.diag(et, -1)
+    lam, V = torch.linalg.eigh(T)
+    return dt, et, lam, V
+
+
+@pytest.mark.parametrize("n", [20, 128, 400])
+def test_matches_dense_eigh_autograd(cuda, n):
+    import torch
+    d, e = tm.random_uniform(n, 31, 32)
+    g = tm.normal(33, n)
+    G = tm.normal(34, n * n).reshape(n, n)
+    w, Z = _fwd(d, e)
+    dd, de = _bwd(w, Z, g=g, G=G)
+    dt, et, lam, V = _loss_grad_dense(d, e, g, G)
+    Zc = Z.cpu().numpy()
+    s = np.sign(np.einsum("ij,ij->j", V.detach().numpy(), Zc))
+    loss = (torch.tensor(g) * lam).sum() + (torch.tensor(G) * (V * torch.tensor(s))).sum()
+    loss.backward()
+    scale = max(np.abs(dt.grad.numpy()).max(), 1.0)
+    assert np.max(np.abs(dd - dt.grad.numpy())) <= 1e-8 * scale
+    assert np.max(np.abs(de - et.grad.numpy())) <= 1e-8 * scale
+
+
+@pytest.mark.parametrize("n", [64, 512])
+def test_central_finite_differences(cuda, n):
+    import torch
+    d, e = tm.random_uniform(n, 41, 42)
+    g = tm.normal(43, n)
+    G = tm.normal(44, n * n).reshape(n, n)
+    w, Z = _fwd(d, e)
+    Z0 = Z.cpu().numpy()
+    dd, de = _bwd(w, Z, g=g, G=G)
+
+    def loss(dv, ev):
+        wv, Zv = _fwd(dv, ev)
+        Zv = Zv.cpu().numpy()
+        Zv = Zv * np.sign(np.einsum("ij,ij->j", Z0, Zv))[None, :]
+        return float(g @ wv.cpu().numpy() + (G * Zv).sum())
+
+    h = 1e-6
+    rel = []
+    for k in range(3):
+        vd = tm.normal(500 + 2 * k, n)
+        ve = tm.normal(501 + 2 * k, n - 1)
+        fd = (loss(d + h * vd, e + h * ve) - loss(d - h * vd, e - h * ve)) / (2 * h)
+        an = float(dd @ vd + de @ ve)
+        rel.append(abs(fd - an) / max(abs(an), 1e-300))
+    # FD truncation error scales like (h / gap)^2; random matrices of this size have gaps
+    # of ~1e-3 or larger, so 1e-6 relative agreement is expected
+    assert max(rel) <= 1e-6, rel
+
+
+def test_fd_against_oracle_forward(cuda):
+    # the backward pinned to finite differences of the CPU oracle's eigen-decomposition
+    import torch
+    n = 40
+    d, e = tm.random_uniform(n, 61, 62)
+    g = tm.normal(63, n)
+    G = tm.normal(64, n * n).reshape(n, n)
+    w, Z = _fwd(d, e)
+    Z0 = Z.cpu().numpy()
+    dd, de = _bwd(w, Z, g=g, G=G)
+
+    def loss(dv, ev):
+        wv = oracle.eigvals(dv, ev)
+        Zv = oracle.eigvecs(dv, ev, wv)
+        Zv = Zv * np.sign(np.einsum("ij,ij->j", Z0, Zv))[None, :]
+        return float(g @ wv + (G * Zv).sum())
+
+    h = 1e-6
+    vd = tm.normal(70, n)
+    ve = tm.normal(71, n - 1)
+    fd = (loss(d + h * vd, e + h * ve) - loss(d - h * vd, e - h * ve)) / (2 * h)
+    an = float(dd @ vd + de @ ve)
+    assert abs(fd - an) <= 1e-6 * abs(an)
+
+
+def test_autograd_function(cuda):
+    import torch
+    import paper_1401_4950_gb300 as mr3
+    n = 100
+    d, e = tm.random_uniform(n, 81, 82)
+    dt = torch.tensor(d, device="cuda", requires_grad=True)
+    et = torch.tensor(e, device="cuda", requires_grad=True)
+    w, Z = mr3.eigh_tridiagonal(dt, et)
+    (w.sum()).backward()
+    assert torch.allclose(dt.grad, torch.ones_like(dt), atol=1e-12)
+    assert torch.max(torch.abs(et.grad)).item() <= 1e-12

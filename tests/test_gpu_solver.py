@@ -1,0 +1,182 @@
+"""Parity of the CUDA MRRR path (through the C ABI) with the CPU oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import testmats as tm
+from _checks import EPS, check_eigenpairs, tnorm_of
+
+pytestmark = pytest.mark.gpu
+
+
+def _solve(d, e, **kw):
+    import torch
+    import paper_1401_4950_gb300 as mr3
+    dt = torch.tensor(np.asarray(d, dtype=np.float64), device="cuda")
+    et = torch.tensor(np.asarray(e, dtype=np.float64) if len(e) else np.zeros(1), device="cuda")
+    w, Z, info = mr3.stemr(dt, et, **kw)
+    torch.cuda.synchronize()
+    return w.cpu().numpy(), Z.cpu().numpy(), info
+
+
+CASES = [("random", 1), ("random", 2), ("random", 3), ("random", 10), ("random", 37),
+         ("random", 100), ("random", 1000), ("one_two_one", 2), ("one_two_one", 100),
+         ("one_two_one", 1000), ("wilkinson", 21), ("wilkinson", 64), ("wilkinson", 1001),
+         ("glued_wilkinson", 42), ("glued_wilkinson", 1000), ("clement", 50), ("clement", 501),
+         ("legendre", 300), ("laguerre", 300), ("hermite", 400)]
+
+
+@pytest.mark.parametrize("kind,n", CASES)
+def test_all_eigenpairs_match_oracle(cuda, kind, n):
+    d, e = tm.make(kind, n, seed=101)
+    w, Z, info = _solve(d, e)
+    assert info["m"] == n and w.shape == (n,) and Z.shape == (n, n)
+    check_eigenpairs(d, e, w, Z)
+
+
+@pytest.mark.parametrize("il,iu", [(1, 1), (1, 17), (40, 60), (100, 200), (190, 200), (200, 200)])
+def test_index_range(cuda, il, iu):
+    d, e = tm.random_uniform(200, 5, 6)
+    w, Z, info = _solve(d, e, rng="I", il=il, iu=iu)
+    assert w.shape == (iu - il + 1,)
+    check_eigenpairs(d, e, w, Z, il=il, iu=iu)
+
+
+@pytest.mark.parametrize("vl,vu", [(-0.5, 0.5), (-10.0, 10.0), (0.3, 0.31), (5.0, 6.0)])
+def test_value_range(cuda, vl, vu):
+    d, e = tm.random_uniform(300, 7, 8)
+    il, iu = oracle.index_range(d, e, "V", vl=vl, vu=vu)
+    w, Z, info = _solve(d, e, rng="V", vl=vl, vu=vu)
+    assert w.shape == (max(iu - il + 1, 0),)
+    if iu >= il:
+        check_eigenpairs(d, e, w, Z, il=il, iu=iu)
+
+
+def test_value_range_boundaries_are_half_open(cuda):
+    d, e = tm.clement(9)  # eigenvalues -8, -6, ..., 8
+    w, Z, _ = _solve(d, e, rng="V", vl=-6.0 + 1e-9, vu=2.0 + 1e-9)
+    assert np.allclose(w, [-4.0, -2.0, 0.0, 2.0], atol=1e-12)
+
+
+def _split_matrix():
+    d1, e1 = tm.random_uniform(40, 1, 2)
+    d2, e2 = tm.wilkinson(21)
+    d3, e3 = tm.one_two_one(30)
+    d = np.r_[d1, d2, [0.7], d3]
+    e = np.r_[e1, [0.0], e2, [0.0], [0.0], e3]
+    assert len(e) == len(d) - 1
+    return d, e
+
+
+def test_split_matrix_all(cuda):
+    d, e = _split_matrix()
+    w, Z, info = _solve(d, e)
+    assert info["nblocks"] == 4
+    check_eigenpairs(d, e, w, Z)
+    # rows outside an eigenvector's block are exactly zero
+    assert np.count_nonzero(Z) <= 40 * 40 + 21 * 21 + 1 + 30 * 30
+
+
+@pytest.mark.parametrize("il,iu", [(1, 92), (10, 50), (41, 41), (60, 92)])
+def test_split_matrix_index_range(cuda, il, iu):
+    d, e = _split_matrix()
+    w, Z, _ = _solve(d, e, rng="I", il=il, iu=iu)
+    check_eigenpairs(d, e, w, Z, il=il, iu=iu)
+
+
+def test_split_matrix_with_ties(cuda):
+    # two identical blocks: every eigenvalue is double; index ranges split ties by block order
+    d0, e0 = tm.random_uniform(25, 3, 4)
+    d = np.r_[d0, d0]
+    e = np.r_[e0, [0.0], e0]
+    w, Z, _ = _solve(d, e, rng="I", il=10, iu=31)
+    check_eigenpairs(d, e, w, Z, il=10, iu=31, vec_compare=False)
+
+
+def test_small_offdiagonal_splits(cuda):
+    d, e = tm.random_uniform(60, 9, 10)
+    e[20] = 1e-300
+    e[41] = -3e-17
+    w, Z, info = _solve(d, e)
+    assert info["nblocks"] == 3
+    check_eigenpairs(d, e, w, Z, vec_compare=False)
+
+
+def test_diagonal_matrix(cuda):
+    d = np.array([3.0, -1.0, 2.0, 2.0, 0.0])
+    e = np.zeros(4)
+    w, Z, info = _solve(d, e)
+    assert np.array_equal(w, np.sort(d))
+    assert np.allclose(np.abs(Z).sum(axis=0), 1.0)
+
+
+def test_constant_diagonal_tiny_coupling(cuda):
+    n = 200
+    d = np.full(n, 1.0)
+    e = np.full(n - 1, 1e-7)
+    w, Z, _ = _solve(d, e)
+    check_eigenpairs(d, e, w, Z, vec_compare=False)
+
+
+def test_scaled_matrices(cuda):
+    d, e = tm.random_uniform(300, 21, 22)
+    for s in (1e-150, 1e150):
+        w, Z, _ = _solve(d * s, e * s)
+        check_eigenpairs(d * s, e * s, w, Z, vec_compare=False)
+
+
+def test_nonfinite_input_reports_status(cuda):
+    d, e = tm.random_uniform(10, 1, 2)
+    d[3] = np.nan
+    w, Z, info = _solve(d, e)
+    assert info["status"] == 3 and info["m"] == 0
+
+
+def test_deterministic(cuda):
+    d, e = tm.random_uniform(800, 31, 32)
+    w1, Z1, _ = _solve(d, e)
+    w2, Z2, _ = _solve(d, e)
+    assert np.array_equal(w1, w2) and np.array_equal(Z1, Z2)
+
+
+def test_fault_injection_rqi_fallback(cuda):
+    import paper_1401_4950_gb300 as mr3
+    d, e = tm.random_uniform(300, 41, 42)
+    w, Z, info = _solve(d, e, opts=mr3.make_opts(fault_mask=mr3.FAULT_RQI_NOCONV))
+    assert info["bisect_fallbacks"] == 300
+    check_eigenpairs(d, e, w, Z)
+
+
+def test_fault_injection_shift_rejected(cuda):
+    import paper_1401_4950_gb300 as mr3
+    d, e = tm.one_two_one(400)
+    w, Z, info = _solve(d, e, opts=mr3.make_opts(fault_mask=mr3.FAULT_SHIFT_REJECT))
+    assert info["untested_rrr"] == info["new_rrr"] > 0
+    assert info["status"] == 1
+    check_eigenpairs(d, e, w, Z, orth_gate=1e3, vec_compare=False)
+
+
+def test_fault_injection_nan_shift(cuda):
+    import paper_1401_4950_gb300 as mr3
+    d, e = tm.one_two_one(400)
+    w, Z, info = _solve(d, e, opts=mr3.make_opts(fault_mask=mr3.FAULT_NAN_SHIFT))
+    check_eigenpairs(d, e, w, Z, vec_compare=False)
+
+
+def test_host_entry_point(cuda):
+    import paper_1401_4950_gb300 as mr3
+    d, e = tm.random_uniform(500, 51, 52)
+    w, Z, info = mr3.stemr_host(d, e)
+    check_eigenpairs(d, e, w, Z)
+    w2, Z2, _ = _solve(d, e)
+    assert np.array_equal(w, w2) and np.array_equal(Z, Z2)
+
+
+def test_clustered_spectrum_statistics(cuda):
+    # 1-2-1 under gaptol 1e-3: eigenvalues with (pi/(n+1)) cot(theta_k/2) < 1e-3 cluster at
+    # the root, theta_k = pi k/(n+1): about 36% of them at n = 2000 (Ch. 5 clustering tables
+    # report rho ~ 0.4-0.9 for n = 2500-20000)
+    d, e = tm.one_two_one(2000)
+    w, Z, info = _solve(d, e)
+    assert 650 < info["largest_cluster"] < 800 and info["dmax"] >= 2
+    check_eigenpairs(d, e, w, Z, vec_compare=False)
