@@ -53,6 +53,17 @@ int lanes_for(long long nactive, const Opts &o) {
     return L;
 }
 
+// Warp slots (one warp each) for an RQI launch: one per 8-32 singletons, within a
+// scratch budget of cap_bytes (160 doubles per index per warp).
+long long rqi_slots(long long nsingle, int nmax, long long cap_bytes) {
+    int lanes = 32;
+    while (lanes > 8 && nsingle < (long long)lanes * 2 * 152) lanes >>= 1;
+    const long long want = (nsingle + lanes - 1) / lanes;
+    const long long per_slot = 160ll * nmax * (long long)sizeof(double);
+    const long long cap = std::max<long long>(152, cap_bytes / per_slot);
+    return std::min(want, cap);
+}
+
 // Optional per-group device timing: an event pair around every launch group, on the
 // call's stream; durations are read after the final synchronisation.
 struct Prof {
@@ -254,14 +265,10 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
         CK(cudaMemcpyAsync(&hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (hc.nsingle > 0) {
-            long long want = (hc.nsingle + 31) / 32;
-            const long long per_slot = 96ll * nmax * (long long)sizeof(double);
-            long long cap = std::max<long long>(152, scratch_cap_bytes / per_slot);
-            long long slots = std::min(want, cap);
-            slots = (slots + 3) / 4 * 4;
+            long long slots = rqi_slots(hc.nsingle, nmax, scratch_cap_bytes);
             if (slots > scratch_slots) {
                 ws.release(scratch);
-                scratch = ws.get<double>((size_t)slots * 96 * nmax);
+                scratch = ws.get<double>((size_t)slots * 160 * nmax);
                 CKW(ws);
                 scratch_slots = slots;
             }
@@ -303,11 +310,10 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
             CK(cudaMemcpyAsync(&hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
             if (hc.nsingle > 0) {
-                long long slots = std::min<long long>((hc.nsingle + 31) / 32, std::max<long long>(152, scratch_cap_bytes / (96ll * nmax * 8)));
-                slots = (slots + 3) / 4 * 4;
+                long long slots = rqi_slots(hc.nsingle, nmax, scratch_cap_bytes);
                 if (slots > scratch_slots) {
                     ws.release(scratch);
-                    scratch = ws.get<double>((size_t)slots * 96 * nmax);
+                    scratch = ws.get<double>((size_t)slots * 160 * nmax);
                     CKW(ws);
                     scratch_slots = slots;
                 }

@@ -11,6 +11,12 @@ namespace mr3 {
 
 #define FULL_MASK 0xffffffffu
 
+// Offset of the shifts from the cluster's end eigenvalues, in units of eps |lambda|
+// (Alg. "Shifting the spectrum" line 2 suggests 100).
+#ifndef MR3_TAU_OFFSET
+#define MR3_TAU_OFFSET 100.0
+#endif
+
 // ------------------------------------------------------------------ bisection
 
 // Sturm count at x for one node: double-float when the node's copy is exact enough and x
@@ -477,8 +483,8 @@ __global__ void k_shift(int ncluster, const ClusterItem *__restrict__ clusters,
     const double Hq = __shfl_sync(FULL_MASK, H, 16);
 
     // ---- 2. shift candidates
-    const double tau_l0 = Lp - 100.0 * kEps * fabs(Lp);
-    const double tau_r0 = Hq + 100.0 * kEps * fabs(Hq);
+    const double tau_l0 = Lp - MR3_TAU_OFFSET * kEps * fabs(Lp);
+    const double tau_r0 = Hq + MR3_TAU_OFFSET * kEps * fabs(Hq);
     const double W = Hq - Lp;
     const double delta = fmax(100.0 * kEps * fmax(fabs(Lp), fabs(Hq)), 1e-3 * W);
     const double thresh = 8.0 * B.spdiam;
@@ -631,7 +637,7 @@ void launch_shift(int ncluster, const ClusterItem *clusters, const long long *cl
                   const int *jloc, double *lo, double *hi, int max_tries, unsigned fault_mask,
                   DevInfo *info, cudaStream_t s) {
     if (ncluster <= 0) return;
-    const int wpb = 2;
+    const int wpb = 1; // one warp per block: spread the serial trial sweeps over the SMs
     k_shift<<<(ncluster + wpb - 1) / wpb, 32 * wpb, 0, s>>>(ncluster, clusters, cluster_rep, nodes,
                                                            blks, pool, childpool, child_nodes,
                                                            child_tau, cnode, active_list, jloc, lo,

@@ -22,8 +22,9 @@ def _batched(sizes, seed0=900, rng="A", il=None, iu=None, vl=None, vu=None, fill
             db, eb = fill(b, n)
         else:
             db, eb = tm.random_uniform(n, seed0 + 2 * b, seed0 + 2 * b + 1)
-        d[n_off[b]:n_off[b + 1]] = db
-        e[n_off[b]:n_off[b + 1] - 1] = eb
+        if n > 0:
+            d[n_off[b]:n_off[b + 1]] = db
+            e[n_off[b]:n_off[b + 1] - 1] = eb
         mats.append((db, eb))
     dt = torch.tensor(d, device="cuda")
     et = torch.tensor(e, device="cuda")
