@@ -243,7 +243,7 @@ def run_gpu(args, cfg, rank, world):
     g = agg["kernel_ms"]
     groups = {"k_bisect": (g[2] + g[6], agg["kernel_launches"][2] + agg["kernel_launches"][6],
                            5.0 * agg["sturm_steps"]),
-              "k_rqi": (g[4], agg["kernel_launches"][4], 15.0 * agg["twisted_steps"]),
+              "k_rqi": (g[4], agg["kernel_launches"][4], 5.5 * agg["twisted_steps"]),
               "k_shift": (g[5], agg["kernel_launches"][5], 5.0 * agg["shift_steps"])}
     dom = max(groups, key=lambda k: groups[k][0])
     ms, launches, flops = groups[dom]

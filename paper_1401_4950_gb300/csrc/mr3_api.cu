@@ -53,13 +53,12 @@ int lanes_for(long long nactive, const Opts &o) {
     return L;
 }
 
-// Warp slots (one warp each) for an RQI launch: one per 8-32 singletons, within a
-// scratch budget of cap_bytes (160 doubles per index per warp).
+// Warp slots (one warp each) for an RQI launch: one per rqi_singles_per_slot()
+// singletons, within a scratch budget of cap_bytes.
 long long rqi_slots(long long nsingle, int nmax, long long cap_bytes) {
-    int lanes = 32;
-    while (lanes > 8 && nsingle < (long long)lanes * 2 * 152) lanes >>= 1;
-    const long long want = (nsingle + lanes - 1) / lanes;
-    const long long per_slot = 160ll * nmax * (long long)sizeof(double);
+    const int per = rqi_singles_per_slot();
+    const long long want = (nsingle + per - 1) / per;
+    const long long per_slot = (long long)rqi_scratch_per_index() * nmax * (long long)sizeof(double);
     const long long cap = std::max<long long>(152, cap_bytes / per_slot);
     return std::min(want, cap);
 }
@@ -73,19 +72,19 @@ struct Prof {
     std::vector<int> group;
     std::vector<int> nlaunch;
     explicit Prof(bool enabled, cudaStream_t st) : on(enabled), s(st) {}
-    int begin() {
+    int begin(cudaStream_t st = nullptr) {
         if (!on) return -1;
         cudaEvent_t a;
         cudaEventCreate(&a);
-        cudaEventRecord(a, s);
+        cudaEventRecord(a, st ? st : s);
         evs.push_back(a);
         return (int)evs.size() - 1;
     }
-    void end(int tok, int g, int launches) {
+    void end(int tok, int g, int launches, cudaStream_t st = nullptr) {
         if (!on || tok < 0) return;
         cudaEvent_t b;
         cudaEventCreate(&b);
-        cudaEventRecord(b, s);
+        cudaEventRecord(b, st ? st : s);
         evs.push_back(b);
         group.push_back(g);
         nlaunch.push_back(launches);
@@ -210,7 +209,7 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
         return 0;
     }
     // ---- root representations and level-0 intervals
-    double *pool0 = ws.get<double>((size_t)kRepStride * nrows);
+    double *pool0 = ws.get<double>((size_t)kRepStride * nrows + (size_t)kRepPad * nblk);
     int *grid = ws.get<int>(ncols + 64ll * nblk + 1);
     float *f32 = ws.get<float>(2 * nrows);
     Node *nodes0 = ws.get<Node>(nblk);
@@ -247,36 +246,81 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
     prof.end(tk, 2, 3);
     ws.release(f32);
 
-    // ---- level loop
+    // ---- level loop.  The singletons of a level are finished by RQI on a side stream
+    // (ordered after that level's classification by an event) while the main stream goes
+    // on with the level's clusters; the two touch disjoint columns.  The singleton list is
+    // double-buffered, and a level's representation pool is returned only after its RQI.
+    cudaStream_t side = nullptr;
+    CK(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    struct SideGuard {
+        cudaStream_t st;
+        std::vector<cudaEvent_t> evs;
+        ~SideGuard() {
+            if (st) cudaStreamSynchronize(st);
+            for (auto e : evs) cudaEventDestroy(e);
+            if (st) cudaStreamDestroy(st);
+        }
+        cudaEvent_t make() {
+            cudaEvent_t e;
+            cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+            evs.push_back(e);
+            return e;
+        }
+    } guard{side, {}};
+    SingleItem *singles2[2] = {singles, ws.get<SingleItem>(ncols)};
+    CKW(ws);
+    struct Pending { double *pool; Node *nodes; cudaEvent_t done; };
+    std::vector<Pending> pending;   // pools/nodes still read by an RQI launch
+    std::vector<cudaEvent_t> rqi_done(2, nullptr);
     Node *cur_nodes = nodes0;
     double *cur_pool = pool0;
     int ncur = nblk;
     double *scratch = nullptr;
     long long scratch_slots = 0;
-    const long long scratch_cap_bytes = 1ll << 30; // RQI scratch budget per launch
+    const long long scratch_cap_bytes = 2ll << 30; // RQI scratch budget per launch
     int status = 0;
+    auto run_singles = [&](int level, const LevelCounters &hc) -> int {
+        long long slots = rqi_slots(hc.nsingle, nmax, scratch_cap_bytes);
+        if (slots > scratch_slots) {
+            if (scratch) cudaFreeAsync(scratch, side); // after the side stream's last use
+            void *p = nullptr;
+            if (cudaMallocAsync(&p, (size_t)slots * rqi_scratch_per_index() * nmax * sizeof(double), s) != cudaSuccess) {
+                cudaGetLastError();
+                scratch = nullptr;
+                return MR3_EOOM;
+            }
+            scratch = (double *)p;
+            scratch_slots = slots;
+        }
+        cudaEvent_t ready = guard.make();
+        cudaEventRecord(ready, s);
+        cudaStreamWaitEvent(side, ready, 0);
+        const int tq = prof.begin(side);
+        launch_rqi(hc.nsingle, singles2[level & 1], cur_nodes, blks, dmats, cur_pool, jloc, lo, hi,
+                   gapl, gapr, d, e, w, Z, scratch, (int)slots, nmax, o.max_rqi, o.fault_mask,
+                   work, dinfo, side);
+        prof.end(tq, 4, 1, side);
+        cudaEvent_t done = guard.make();
+        cudaEventRecord(done, side);
+        rqi_done[level & 1] = done;
+        return 0;
+    };
     for (int level = 0;; ++level) {
+        // the singleton buffer of this parity was last read by the RQI two levels back
+        if (rqi_done[level & 1]) { cudaStreamWaitEvent(s, rqi_done[level & 1], 0); rqi_done[level & 1] = nullptr; }
         CK(cudaMemsetAsync(ctr, 0, sizeof(LevelCounters), s));
         tk = prof.begin();
-        launch_classify(ncur, cur_nodes, blks, lo, hi, o.gaptol, gapl, gapr, singles, clusters,
-                        crep, cnode, ctr, dinfo, s);
+        launch_classify(ncur, cur_nodes, blks, lo, hi, o.gaptol, gapl, gapr, singles2[level & 1],
+                        clusters, crep, cnode, ctr, dinfo, s);
         prof.end(tk, 3, 1);
         LevelCounters hc;
         CK(cudaMemcpyAsync(&hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
+        cudaEvent_t level_rqi = nullptr;
         if (hc.nsingle > 0) {
-            long long slots = rqi_slots(hc.nsingle, nmax, scratch_cap_bytes);
-            if (slots > scratch_slots) {
-                ws.release(scratch);
-                scratch = ws.get<double>((size_t)slots * 160 * nmax);
-                CKW(ws);
-                scratch_slots = slots;
-            }
-            tk = prof.begin();
-            launch_rqi(hc.nsingle, singles, cur_nodes, blks, dmats, cur_pool, jloc, lo, hi, gapl,
-                       gapr, d, e, w, Z, scratch, (int)slots, nmax, o.max_rqi, o.fault_mask, work,
-                       dinfo, s);
-            prof.end(tk, 4, 1);
+            const int rc = run_singles(level, hc);
+            if (rc) return rc;
+            level_rqi = rqi_done[level & 1];
         }
         if (hc.ncluster == 0) break;
         const bool at_cap = (level + 1 >= o.max_depth);
@@ -295,8 +339,14 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
                       next_nodes, blks, next_pool, jloc, lo, hi, rtol, tau, dinfo, s);
         prof.end(tk, 6, 1);
         ws.release(next_active);
-        if (cur_pool != pool0) ws.release(cur_pool);
-        if (cur_nodes != nodes0) ws.release(cur_nodes);
+        // return representations no longer read: older levels whose RQI has finished
+        for (auto &pnd : pending) {
+            if (pnd.done) cudaStreamWaitEvent(s, pnd.done, 0);
+            if (pnd.pool != pool0) ws.release(pnd.pool);
+            if (pnd.nodes != nodes0) ws.release(pnd.nodes);
+        }
+        pending.clear();
+        pending.push_back({cur_pool, cur_nodes, level_rqi});
         cur_pool = next_pool;
         cur_nodes = next_nodes;
         ncur = hc.ncluster;
@@ -304,26 +354,26 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
             // Depth cap: the remaining cluster members are finished as singletons of their
             // current representation (accuracy no longer guaranteed; flagged).
             status = MR3_SDEPTH;
+            const int lv = level + 1;
+            if (rqi_done[lv & 1]) { cudaStreamWaitEvent(s, rqi_done[lv & 1], 0); rqi_done[lv & 1] = nullptr; }
             CK(cudaMemsetAsync(ctr, 0, sizeof(LevelCounters), s));
-            launch_classify(ncur, cur_nodes, blks, lo, hi, -1e308, gapl, gapr, singles, clusters,
-                            crep, cnode, ctr, dinfo, s);
+            launch_classify(ncur, cur_nodes, blks, lo, hi, -1e308, gapl, gapr, singles2[lv & 1],
+                            clusters, crep, cnode, ctr, dinfo, s);
             CK(cudaMemcpyAsync(&hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
             if (hc.nsingle > 0) {
-                long long slots = rqi_slots(hc.nsingle, nmax, scratch_cap_bytes);
-                if (slots > scratch_slots) {
-                    ws.release(scratch);
-                    scratch = ws.get<double>((size_t)slots * 160 * nmax);
-                    CKW(ws);
-                    scratch_slots = slots;
-                }
-                launch_rqi(hc.nsingle, singles, cur_nodes, blks, dmats, cur_pool, jloc, lo, hi,
-                           gapl, gapr, d, e, w, Z, scratch, (int)slots, nmax, o.max_rqi, o.fault_mask,
-                           work, dinfo, s);
+                const int rc = run_singles(lv, hc);
+                if (rc) return rc;
             }
             break;
         }
     }
+    // the main stream resumes after every singleton launch
+    for (auto ev : rqi_done)
+        if (ev) cudaStreamWaitEvent(s, ev, 0);
+    for (auto &pnd : pending)
+        if (pnd.done) cudaStreamWaitEvent(s, pnd.done, 0);
+    if (scratch) cudaFreeAsync(scratch, s);
     // ---- output order: sort the eigenpairs of matrices whose eigenvalues came out of order
     int *oflags = ws.get<int>(nmat);
     CKW(ws);

@@ -3,10 +3,14 @@
 // Notation follows the thesis (Ch. 3): a representation is an N-representation of a
 // lower bidiagonal factorization L D L^T with d (n pivots) and l (n-1 multipliers);
 // the derived data dl_i = d_i l_i and dll_i = d_i l_i^2 are kept beside d (remark on
-// Alg. NegCount on LDL^T, App. B).  A representation of order n occupies kRepStride * n
-// doubles of a pool starting at an even double offset: d at [0, n), dl at [n, 2n), dll at
-// [2n, 3n), and from the even offset rep_df_offset(n) a double-float copy
-// {d.h, d.l, dll.h, dll.l} (one 16-byte aligned float4 per index) for the bisection.
+// Alg. NegCount on LDL^T, App. B).  A representation of order n occupies rep_size(n)
+// doubles of a pool starting at an even double offset:
+//   d at [0, n), dl at [n, 2n), dll at [2n, 3n);
+//   from the even offset rep_df_offset(n), a double-float copy {d.h, d.l, dll.h, dll.l}
+//   (one 16-byte aligned float4 per index) for the bisection;
+//   from rep_q_offset(n), the prefix products Q_i = prod_{k<i} (-dl_k) as a mantissa
+//   Qm_i in [1, 2) (signed), its reciprocal iQm_i and an int exponent Qe_i (the twisted
+//   solve of the singletons multiplies them instead of running a product chain).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -15,8 +19,11 @@ namespace mr3 {
 
 constexpr double kEps = 1.1102230246251565e-16;     // unit roundoff 2^-53
 constexpr double kSafmin = 2.2250738585072014e-308; // underflow threshold omega
-constexpr int kRepStride = 6;                       // doubles per index in a representation
+constexpr int kRepStride = 8; // doubles per index in a representation (plus kRepPad)
+constexpr int kRepPad = 4;
+__host__ __device__ __forceinline__ long long rep_size(int n) { return (long long)kRepStride * n + kRepPad; }
 __host__ __device__ __forceinline__ long long rep_df_offset(int n) { return 3ll * n + (n & 1); }
+__host__ __device__ __forceinline__ long long rep_q_offset(int n) { return rep_df_offset(n) + 2ll * n; }
 
 // One input matrix of a (possibly batched) solve.
 struct MatDesc {
@@ -224,6 +231,74 @@ __device__ __forceinline__ int negcount_T_f32(int n, const float *__restrict__ a
         sp = sc;
     }
     return cnt;
+}
+
+// Q_i = prod_{k<i} (-dl_k), i = 0..n-1, for a representation at rep (warp-collective: a
+// chunk of indices per lane, an exclusive product scan over the lanes, then each lane
+// walks its chunk).  Stored as Qm (signed mantissa in [1, 2)), iQm = 1/Qm, Qe (exponent).
+__device__ __forceinline__ void split_exp(double x, double &m, int &e) {
+    if (is_zero(x) || !is_finite(x)) { m = x; e = 0; return; }
+    const int ex = biased_exp(x);
+    if (ex == 0) { x *= 0x1p+600; e = biased_exp(x) - 1023 - 600; m = x * pow2i(-(biased_exp(x) - 1023)); return; }
+    e = ex - 1023;
+    m = x * pow2i(-e);
+}
+
+__device__ __forceinline__ void build_prefix(int n, double *rep) {
+    const int lane = threadIdx.x & 31;
+    const double *dl = rep + n;
+    double *Qm = rep + rep_q_offset(n);
+    double *iQm = Qm + n;
+    int *Qe = (int *)(iQm + n);
+    const int ch = (n + 31) / 32;
+    const int i0 = min(lane * ch, n), i1 = min(i0 + ch, n);
+    // product of -dl_k over this lane's chunk (k < n-1)
+    double m = 1.0;
+    int e = 0;
+    for (int k = i0; k < i1 && k < n - 1; ++k) {
+        double t;
+        int te;
+        split_exp(-dl[k], t, te);
+        m *= t;
+        e += te;
+        double mm;
+        int me;
+        split_exp(m, mm, me);
+        m = mm;
+        e += me;
+    }
+    // exclusive scan of (m, e) over lanes
+    double pm = m;
+    int pe = e;
+    for (int o = 1; o < 32; o <<= 1) {
+        const double ym = __shfl_up_sync(0xffffffffu, pm, o);
+        const int ye = __shfl_up_sync(0xffffffffu, pe, o);
+        if (lane >= o) {
+            double mm;
+            int me;
+            split_exp(pm * ym, mm, me);
+            pm = mm;
+            pe = pe + ye + me;
+        }
+    }
+    double xm = __shfl_up_sync(0xffffffffu, pm, 1);
+    int xe = __shfl_up_sync(0xffffffffu, pe, 1);
+    if (lane == 0) { xm = 1.0; xe = 0; }
+    for (int i = i0; i < i1; ++i) {
+        Qm[i] = xm;
+        Qe[i] = xe;
+        iQm[i] = 1.0 / xm;
+        if (i < n - 1) {
+            double t;
+            int te;
+            split_exp(-dl[i], t, te);
+            double mm;
+            int me;
+            split_exp(xm * t, mm, me);
+            xm = mm;
+            xe = xe + te + me;
+        }
+    }
 }
 
 } // namespace mr3

@@ -72,4 +72,9 @@ void launch_rqi(int nsingle, const SingleItem *singles, const Node *nodes, const
                 int max_rqi, unsigned fault_mask, int *work_counter, DevInfo *info,
                 cudaStream_t s);
 
+// Scratch doubles per index per warp slot of the singleton kernel, and singletons a warp
+// slot holds at a time.
+int rqi_scratch_per_index();
+int rqi_singles_per_slot();
+
 } // namespace mr3

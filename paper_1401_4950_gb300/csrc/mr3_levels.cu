@@ -304,7 +304,7 @@ __global__ void k_classify(int nnode, const Node *__restrict__ nodes, const BlkD
             if (mc) {
                 cbase = atomicAdd(&ctr->ncluster, __popc(mc));
                 pbase = atomicAdd((unsigned long long *)&ctr->pool_need,
-                                  (unsigned long long)((long long)kRepStride * nb * __popc(mc)));
+                                  (unsigned long long)(rep_size(nb) * __popc(mc)));
             }
         }
         sbase = __shfl_sync(FULL_MASK, sbase, 0);
@@ -337,7 +337,7 @@ __global__ void k_classify(int nnode, const Node *__restrict__ nodes, const BlkD
             it.lnb = (gs > N.c0) ? hi[gs - 1] : N.lnb;
             it.rnb = (c < N.c1) ? ln : N.rnb;
             clusters[cbase + k] = it;
-            cluster_rep[cbase + k] = pbase + (long long)kRepStride * nb * k;
+            cluster_rep[cbase + k] = pbase + rep_size(nb) * k;
             maxsize = max(maxsize, size);
             nclus++;
         }
@@ -605,6 +605,8 @@ __global__ void k_shift(int ncluster, const ClusterItem *__restrict__ clusters,
         __syncwarp();
     }
     dfok = __all_sync(FULL_MASK, dfok);
+    __syncwarp();
+    build_prefix(n, cd);
 
     // ---- 4. child node
     for (int c = p + lane; c <= q; c += 32) {

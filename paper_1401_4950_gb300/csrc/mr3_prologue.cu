@@ -224,7 +224,7 @@ __global__ void k_blocks_from_flags(long long nrows, const int *flags, const int
     B.mat = b;
     B.roff = (int)(i - mats[b].off);
     B.n = 0;
-    B.rep = (long long)kRepStride * i;
+    B.rep = (long long)kRepStride * i + (long long)kRepPad * id;
     B.dfok = 0;
     B.j0 = 1;
     B.j1 = 0;
@@ -548,6 +548,8 @@ __global__ void k_root(int nblk, BlkDesc *blks, const double *__restrict__ D,
         dfok &= df_safe(dp) && df_safe(dll);
     }
     dfok = __all_sync(FULL_MASK, dfok);
+    __syncwarp();
+    build_prefix(n, reg0);
     if (lane == 0) { blks[b].mu = mu; blks[b].dfok = dfok ? 1 : 0; }
 }
 

@@ -8,18 +8,23 @@ namespace mr3 {
 
 #define FULL_MASK 0xffffffffu
 
-// Per-thread scratch with the 32 lanes of a warp interleaved, so that the accesses of a
-// warp at step i are contiguous: per index five 256-byte rows (a_i, c_{i-1}, h_i,
-// d_i f_{i+1}, and the two scale exponents as an int2).
+// A team of kTeam lanes finishes one singleton; a warp holds kTeams teams.  Lanes 0 and 1
+// of a team run the two serial recurrences of a twisted factorization, after which all
+// lanes of the team share the element-wise work (twist index, solve, normalisation).
+constexpr int kTeam = 8;
+constexpr int kTeams = 32 / kTeam;
+constexpr int kScratchPerIndex = 5 * kTeams; // doubles per index per warp slot
+
+// Scratch of one team: per index five values (a_i, c_{i-1}, h_i, d_i f_{i+1}, and the two
+// scale exponents as an int2), interleaved with the other teams of the warp.
 struct Scratch {
-    double *base;
-    __device__ __forceinline__ double &A(int i) const { return base[(size_t)i * 160]; }
-    __device__ __forceinline__ double &C(int i) const { return base[(size_t)i * 160 + 32]; }
-    __device__ __forceinline__ double &H(int i) const { return base[(size_t)i * 160 + 64]; }
-    __device__ __forceinline__ double &Q(int i) const { return base[(size_t)i * 160 + 96]; }
-    __device__ __forceinline__ int2 &E(int i) const { return *(int2 *)(base + (size_t)i * 160 + 128); }
+    double *base; // warp slot base + team
+    __device__ __forceinline__ double &A(int i) const { return base[(size_t)i * kScratchPerIndex]; }
+    __device__ __forceinline__ double &C(int i) const { return base[(size_t)i * kScratchPerIndex + kTeams]; }
+    __device__ __forceinline__ double &H(int i) const { return base[(size_t)i * kScratchPerIndex + 2 * kTeams]; }
+    __device__ __forceinline__ double &Q(int i) const { return base[(size_t)i * kScratchPerIndex + 3 * kTeams]; }
+    __device__ __forceinline__ int2 &E(int i) const { return *(int2 *)(base + (size_t)i * kScratchPerIndex + 4 * kTeams); }
 };
-constexpr int kScratchPerIndex = 160; // doubles per index per warp slot
 
 // Rescale (x, y) by 2^k so that |x| is near 1 when x leaves [2^-200, 2^200]; returns k.
 __device__ __forceinline__ int rescale2(double &x, double &y) {
@@ -51,281 +56,304 @@ __device__ __forceinline__ float log2abs(double x) {
     return (float)(ex - 1023) + __log2f(mant);
 }
 
-// Getvec (Alg. Getvec) for L D L^T - lam I without divisions in the recurrences.
-// With the homogeneous variables of the Sturm count (see negcount_ldl),
+// Reductions over the kTeam lanes of a team (all 32 lanes call them together).
+__device__ __forceinline__ double team_sum(double v) {
+    for (int o = kTeam / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, kTeam);
+    return v;
+}
+__device__ __forceinline__ void team_argmin(float &key, int &idx) {
+    for (int o = kTeam / 2; o > 0; o >>= 1) {
+        const float k2 = __shfl_xor_sync(0xffffffffu, key, o, kTeam);
+        const int i2 = __shfl_xor_sync(0xffffffffu, idx, o, kTeam);
+        if (k2 < key || (k2 == key && i2 < idx)) { key = k2; idx = i2; }
+    }
+}
+__device__ __forceinline__ void team_argmax_bits(long long &b, int &idx) {
+    for (int o = kTeam / 2; o > 0; o >>= 1) {
+        const long long b2 = __shfl_xor_sync(0xffffffffu, b, o, kTeam);
+        const int i2 = __shfl_xor_sync(0xffffffffu, idx, o, kTeam);
+        if (b2 > b || (b2 == b && i2 < idx)) { b = b2; idx = i2; }
+    }
+}
+
+// Persistent kernel (one warp per block; each team takes one singleton at a time).
+// Per singleton (Alg. S-task): lam = midpoint of [lo, hi]; repeat Getvec; update [lo, hi]
+// from the inertia count; accept when |gamma_r|/||z|| < tol1 gap (tol1 = n eps, gap = the
+// distance to the nearest other eigenvalue) or |gamma_r|/||z||^2 < tol2 |lam| (tol2 = 4 eps),
+// or when the correction stalls at a level tiny against the gap; otherwise apply the
+// Rayleigh quotient correction gamma_r/||z||^2 when its sign points toward the eigenvalue
+// and the result stays in [lo, hi]; else (or after max_rqi Getvecs) bisect to full accuracy
+// and accept after one more Getvec.
+//
+// Getvec (Alg. Getvec) is evaluated without divisions in the recurrences.  With the
+// homogeneous variables of the Sturm count (see negcount_ldl),
 //   forward  (dstqds):  c_i = d_i c_{i-1} + a_i,      a_{i+1} = dll_i a_i - lam c_i,
 //                       d+_i = c_i / c_{i-1},          s_i = a_i / c_{i-1};
 //   backward (dqds, read as in the design notes: omega-_{i+1} = p_{i+1} + dll_i):
 //                       h_i = dll_i h_{i+1} + f_{i+1}, f_i = d_i f_{i+1} - lam h_i,
 //                       omega-_{i+1} = h_i / h_{i+1},  p_i = f_i / h_i,
-// started from c_{-1} = 1, a_0 = -lam, h_{n-1} = 1, f_{n-1} = d_{n-1} - lam.  Then
+// from c_{-1} = 1, a_0 = -lam, h_{n-1} = 1, f_{n-1} = d_{n-1} - lam, so that
 //   gamma_i = s_i + d_i p_{i+1}/omega-_{i+1} = (a_i h_i + c_{i-1} d_i f_{i+1}) / (c_{i-1} h_i),
-//   gamma_{n-1} = d+_{n-1},
-// where numerator and denominator share one scale.  The twisted solve N_r^T z = e_r,
-// z_i = -l+_i z_{i+1} (i < r), z_{i+1} = -u-_i z_i (i >= r), with l+_i = dl_i c_{i-1}/c_i and
-// u-_i = dl_i h_{i+1}/h_i, telescopes to
-//   z_i = c_{i-1}/c_{r-1} prod_{k=i}^{r-1} (-dl_k)   (i < r),
-//   z_i = h_i/h_r prod_{k=r}^{i-1} (-dl_k)           (i > r),
-// which also covers the zero-pivot rule of Alg. Getvec without a special case.  (a, c)
-// and (f, h) carry power-of-two scales tracked as integer exponents.
-// Pass 1 runs the forward and backward recurrences interleaved (two independent chains),
-// pass 2 ranks |gamma_i| in the log domain (full factorization only), pass 3 solves
-// outward from r in both directions at once.
-//  r < 0 : full factorization, r = argmin |gamma_i|; the count is NegCount(LDL^T, lam).
-//  r >= 0: only the twisted factorization at r; the count is the inertia of
-//          diag(d+_0..d+_{r-1}, gamma_r, omega-_{r+1}..omega-_{n-1}).
-__device__ void getvec_h(int n, const double *__restrict__ d, const double *__restrict__ dl,
-                         const double *__restrict__ dll, double lam, int &r, const Scratch &S,
-                         double *zc, double &gamma, double &nrm2, int &negc, int &imax,
-                         unsigned long long &steps) {
-    const bool full = r < 0;
-    const bool need_last = full || r == n - 1;  // c_{n-1} (gamma_{n-1}) needed
-    const int fend = full ? n - 1 : r;            // forward stores indices 0..fend
-    const int blow = full ? 0 : r;                // backward computes h_i for blow..n-2
-    // ---- pass 1: forward (index i = t) and backward (index n-2-t) interleaved
-    double a = -lam, cp = 1.0;
-    int F = 0, sp = 0, cntf = 0;
-    double c_last = 1.0, cprev_last = 1.0;
-    double f = __ldg(d + n - 1) - lam, h = 1.0;
-    int G = 0, sh = 0, cntb = 0;
-    const int nf = fend + 1, nb = n - 1 - blow;
-    const int T = max(nf, nb);
-    for (int t = 0; t < T; ++t) {
-        if (t < nf) {
-            const int i = t;
-            S.A(i) = a;
-            S.C(i) = cp;
-            S.E(i).x = F;
-            if (i < fend || need_last) {
-                double c = fma(__ldg(d + i), cp, a);
-                if (is_zero(c)) c = -cp * 0x1p-80;
-                const int sc = sign_bit(c);
-                if (full || i < r) cntf += sc ^ sp;
-                if (i == n - 1) {
-                    c_last = c;
-                    cprev_last = cp;
-                } else {
-                    const double tt = __ldg(dll + i) * a;
-                    a = fma(-lam, c, tt);
-                    F -= rescale2(c, a);
-                    cp = c;
-                    sp = sc;
-                }
-            }
-        }
-        if (t < nb) {
-            const int i = n - 2 - t;
-            double hi = fma(__ldg(dll + i), h, f);
-            if (is_zero(hi)) hi = -h * 0x1p-80;
-            const int sgh = sign_bit(hi);
-            cntb += sgh ^ sh; // omega-_{i+1} = h_i / h_{i+1}
-            const double df = __ldg(d + i) * f;
-            f = fma(-lam, hi, df);
-            S.H(i) = hi;
-            S.Q(i) = df;
-            S.E(i).y = G;
-            G -= rescale2(hi, f);
-            h = hi;
-            sh = sgh;
-        }
-    }
-    steps += (unsigned long long)(nf + nb);
-    // ---- pass 2: gamma and the twist index
-    double gnum, gden;
-    int cnt;
-    if (full) {
-        float best = log2abs(c_last) - log2abs(cprev_last);
-        if (!(best == best)) best = 3.0e38f;
-        int rr = n - 1;
-#pragma unroll 4
-        for (int i = 0; i < n - 1; ++i) {
-            const double ci = S.C(i), hi = S.H(i);
-            const double num = fma(S.A(i), hi, ci * S.Q(i));
-            const float key = log2abs(num) - log2abs(ci * hi);
-            if (key <= best) {
-                if (key < best || i < rr) rr = i;
-                best = key;
-            }
-        }
-        r = rr;
-        cnt = cntf;
-    } else {
-        cnt = cntf + cntb;
-    }
-    if (r == n - 1) {
-        gnum = c_last;
-        gden = cprev_last;
-    } else {
-        const double ci = S.C(r), hi = S.H(r);
-        gnum = fma(S.A(r), hi, ci * S.Q(r));
-        gden = ci * hi;
-    }
-    gamma = gnum / gden;
-    if (!full) cnt += sign_bit(gamma);
-    negc = cnt;
-    // ---- pass 3: solve N_r^T z = e_r (z_r = 1), both directions at once
-    const int rf = S.E(r).x;                               // scale of c_{r-1}
-    const double icr = 1.0 / S.C(r);                        // 1 / c_{r-1} (stored)
-    const double ihr = (r < n - 1) ? 1.0 / S.H(r) : 1.0;    // 1 / h_r (stored)
-    const int rg = (r < n - 1) ? S.E(r).y : 0;
-    zc[r] = 1.0;
-    double ss0 = 1.0, ss1 = 0.0;
-    long long zmaxb = 0x3ff0000000000000ll; // bits of 1.0
-    int im = r;
-    double Pd = 1.0, Pu = 1.0;
-    int EPd = 0, EPu = 0;
-    const int ndown = r, nup = n - 1 - r;
-    const int T3 = max(ndown, nup);
-    for (int t = 0; t < T3; ++t) {
-        if (t < ndown) {
-            const int i = r - 1 - t;
-            Pd *= -__ldg(dl + i);
-            if ((unsigned)(biased_exp(Pd) - (1023 - 200)) > 400u && !is_zero(Pd)) {
-                const int k = 1023 - biased_exp(Pd);
-                Pd *= pow2i(k);
-                EPd -= k;
-            }
-            const double zi = scale2(Pd * S.C(i) * icr, EPd + S.E(i).x - rf);
-            zc[i] = zi;
-            ss0 = fma(zi, zi, ss0);
-            const long long zb = __double_as_longlong(zi) & 0x7fffffffffffffffll;
-            if (zb > zmaxb) { zmaxb = zb; im = i; }
-        }
-        if (t < nup) {
-            const int i = r + 1 + t;
-            Pu *= -__ldg(dl + i - 1);
-            if ((unsigned)(biased_exp(Pu) - (1023 - 200)) > 400u && !is_zero(Pu)) {
-                const int k = 1023 - biased_exp(Pu);
-                Pu *= pow2i(k);
-                EPu -= k;
-            }
-            const double hh = (i < n - 1) ? S.H(i) : 1.0;
-            const int gi = (i < n - 1) ? S.E(i).y : 0;
-            const double zi = scale2(Pu * hh * ihr, EPu + gi - rg);
-            zc[i] = zi;
-            ss1 = fma(zi, zi, ss1);
-            const long long zb = __double_as_longlong(zi) & 0x7fffffffffffffffll;
-            if (zb > zmaxb || (zb == zmaxb && i < im)) { zmaxb = zb; im = i; }
-        }
-    }
-    nrm2 = ss0 + ss1;
-    imax = im;
-    steps += (unsigned long long)n;
-}
-
-// Persistent kernel: each warp takes 32 consecutive singletons at a time.  Per singleton
-// (Alg. S-task): lam = midpoint of [lo, hi]; repeat Getvec; update [lo, hi] from the count;
-// accept when |gamma_r|/||z|| < tol1 gap (tol1 = n eps, gap = distance to the nearest
-// other eigenvalue) or |gamma_r|/||z||^2 < tol2 |lam| (tol2 = 2 eps); otherwise apply the
-// Rayleigh quotient correction gamma_r/||z||^2 when its sign points toward the eigenvalue
-// and the result stays in [lo, hi]; else (or after max_rqi Getvecs) bisect to full
-// accuracy and accept after one more Getvec.  The eigenvalue returned is the Rayleigh
-// quotient lam + gamma_r/||z||^2 (when inside [lo, hi]) plus the node's shift sigma; z is
-// normalised with its largest entry positive.
+//   gamma_{n-1} = d+_{n-1}.
+// The twisted solve N_r^T z = e_r (z_i = -l+_i z_{i+1} for i < r, z_{i+1} = -u-_i z_i for i >= r,
+// l+_i = dl_i c_{i-1}/c_i, u-_i = dl_i h_{i+1}/h_i) telescopes to
+//   z_i = (Q_r / Q_i) c_{i-1} / c_{r-1}  (i < r),   z_i = (Q_i / Q_r) h_i / h_r  (i > r),
+// with the representation's prefix products Q_i = prod_{k<i} (-dl_k); this covers the
+// zero-pivot rule of Alg. Getvec and makes every element independent.  (a, c) and (f, h)
+// carry power-of-two scales tracked as integer exponents.  The count returned with a full
+// factorization is NegCount(LDL^T, lam); with a given twist index r it is the inertia of
+// diag(d+_0..d+_{r-1}, gamma_r, omega-_{r+1}..omega-_{n-1}).  The eigenvalue returned is the
+// Rayleigh quotient of z with respect to the input T (accuracy remark 5, Sec. 3.1.2), which
+// removes the bias of the root's random perturbation.
 __global__ void __launch_bounds__(32) k_rqi(int nsingle, const SingleItem *__restrict__ singles,
-                                             const Node *__restrict__ nodes,
-                                             const BlkDesc *__restrict__ blks,
-                                             const MatDesc *__restrict__ mats,
-                                             const double *__restrict__ pool,
-                                             const int *__restrict__ jloc,
-                                             const double *__restrict__ lo,
-                                             const double *__restrict__ hi,
-                                             const double *__restrict__ gapl,
-                                             const double *__restrict__ gapr,
-                                             const double *__restrict__ Din,
-                                             const double *__restrict__ Ein, double *w, double *Z,
-                                             double *scratch, int nmax, int max_rqi,
-                                             unsigned fault_mask, int *work_counter, int lanes,
-                                             DevInfo *info) {
+                                            const Node *__restrict__ nodes,
+                                            const BlkDesc *__restrict__ blks,
+                                            const MatDesc *__restrict__ mats,
+                                            const double *__restrict__ pool,
+                                            const int *__restrict__ jloc,
+                                            const double *__restrict__ lo,
+                                            const double *__restrict__ hi,
+                                            const double *__restrict__ gapl,
+                                            const double *__restrict__ gapr,
+                                            const double *__restrict__ Din,
+                                            const double *__restrict__ Ein, double *w, double *Z,
+                                            double *scratch, int nmax, int max_rqi,
+                                            unsigned fault_mask, int *work_counter,
+                                            DevInfo *info) {
     const int lane = threadIdx.x & 31;
-    const int slot = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int team = lane / kTeam, k = lane % kTeam, tbase = team * kTeam;
+    const int slot = blockIdx.x;
     Scratch S;
-    S.base = scratch + (size_t)slot * kScratchPerIndex * (size_t)nmax + lane;
+    S.base = scratch + (size_t)slot * kScratchPerIndex * (size_t)nmax + team;
     unsigned long long steps = 0, iters = 0;
     int itmax = 0, nfb = 0, ncap = 0;
     for (;;) {
         int chunk = 0;
-        if (lane == 0) chunk = atomicAdd(work_counter, lanes);
+        if (lane == 0) chunk = atomicAdd(work_counter, kTeams);
         chunk = __shfl_sync(FULL_MASK, chunk, 0);
         if (chunk >= nsingle) break;
-        const int idx = chunk + lane;
-        if (lane < lanes && idx < nsingle) {
+        const int idx = chunk + team;
+        const bool active = idx < nsingle;
+        // ---- singleton data (every lane of the team holds a copy)
+        int c = 0, n = 1, j = 1;
+        const double *d = pool, *dl = pool, *dll = pool, *Qm = pool, *iQm = pool;
+        const int *Qe = (const int *)pool;
+        double l = 0.0, h = 0.0, gap = 1.0, sigma = 0.0;
+        double *zc = Z;
+        const double *td = Din, *te = Ein;
+        if (active) {
             const SingleItem it = singles[idx];
-            const int c = it.col;
+            c = it.col;
             const Node N = nodes[it.node];
             const BlkDesc B = blks[N.blk];
             const MatDesc M = mats[B.mat];
-            const int n = B.n;
-            const double *d = pool + N.rep, *dl = d + n, *dll = d + 2 * n;
-            const int j = jloc[c];
-            double l = lo[c], h = hi[c];
-            double gap = fmin(gapl[c], gapr[c]);
+            n = B.n;
+            d = pool + N.rep;
+            dl = d + n;
+            dll = d + 2 * n;
+            Qm = d + rep_q_offset(n);
+            iQm = Qm + n;
+            Qe = (const int *)(iQm + n);
+            j = jloc[c];
+            l = lo[c];
+            h = hi[c];
+            gap = fmin(gapl[c], gapr[c]);
             if (!(gap > 0.0)) gap = kSafmin;
-            double *zc = Z + M.zoff + (long long)(c - M.woff) * M.ldz + B.roff;
-            const double tol1 = n * kEps, tol2 = 4.0 * kEps, tol_noise = n * kEps;
-            double lam = l + 0.5 * (h - l);
-            int r = -1, it_n = 0;
-            bool fb = false, capped = false;
-            double gamma = 0.0, nrm2 = 1.0, rqc = 0.0;
-            int negc = 0, imax = 0;
-            double prev_arqc = INFINITY;
-            for (int guard = 0; guard < 64; ++guard) {
-                getvec_h(n, d, dl, dll, lam, r, S, zc, gamma, nrm2, negc, imax, steps);
-                ++it_n;
-                if (negc >= j) h = fmin(h, lam); else l = fmax(l, lam);
-                const double nz = sqrt(nrm2);
-                const double resid = fabs(gamma) / nz;
-                rqc = gamma / nrm2;
-                const bool conv = (resid < tol1 * gap) || (fabs(rqc) < tol2 * fabs(lam));
-                // RQI converges cubically; a correction that no longer shrinks (at least by
-                // half) while tiny against the gap sits at the representation's noise level
-                const bool stalled = it_n >= 2 && fabs(rqc) >= 0.5 * prev_arqc &&
-                                     fabs(rqc) <= 1e-3 * gap;
-                if (fb || ((conv || stalled) && !(fault_mask & MR3_FAULT_RQI_NOCONV))) break;
-                prev_arqc = fabs(rqc);
-                const bool sign_ok = (negc < j) ? (rqc > 0.0) : (rqc < 0.0);
-                const double lnew = lam + rqc;
-                if (it_n < max_rqi && sign_ok && lnew >= l && lnew <= h) {
-                    lam = lnew;
-                    continue;
+            sigma = N.sigma;
+            zc = Z + M.zoff + (long long)(c - M.woff) * M.ldz + B.roff;
+            td = Din + B.off;
+            te = Ein + B.off;
+        }
+        const double tol1 = n * kEps, tol2 = 4.0 * kEps, tol_noise = n * kEps;
+        double lam = l + 0.5 * (h - l);
+        int r = -1, it_n = 0;
+        bool done = !active, fb = false, capped = false;
+        double nrm2 = 1.0, rqc = 0.0, prev_arqc = INFINITY;
+        int imax = 0;
+        for (int guard = 0; guard < 64; ++guard) {
+            if (__all_sync(FULL_MASK, done)) break;
+            const bool full = r < 0;
+            const bool need_last = full || r == n - 1;
+            const int fend = full ? n - 1 : r;
+            const int blow = full ? 0 : r;
+            // ---- pass 1: lane 0 forward recurrence, lane 1 backward recurrence
+            int cntf = 0, cntb = 0;
+            double c_last = 1.0, cprev_last = 1.0;
+            if (!done && k == 0) {
+                double a = -lam, cp = 1.0;
+                int F = 0, sp = 0;
+                for (int i = 0; i <= fend; ++i) {
+                    S.A(i) = a;
+                    S.C(i) = cp;
+                    S.E(i).x = F;
+                    if (i == fend && !need_last) break;
+                    double cc = fma(__ldg(d + i), cp, a);
+                    if (is_zero(cc)) cc = -cp * 0x1p-80;
+                    const int sc = sign_bit(cc);
+                    if (full || i < r) cntf += sc ^ sp;
+                    if (i == n - 1) {
+                        c_last = cc;
+                        cprev_last = cp;
+                        break;
+                    }
+                    const double tt = __ldg(dll + i) * a;
+                    a = fma(-lam, cc, tt);
+                    F -= rescale2(cc, a);
+                    cp = cc;
+                    sp = sc;
                 }
-                // A correction at the level of the rounding noise of the twisted
-                // factorization (|rqc| <= n eps |lam|) cannot improve lam: accept.
-                if (!(fault_mask & MR3_FAULT_RQI_NOCONV) && fabs(rqc) <= tol_noise * fabs(lam)) break;
-                if (it_n >= max_rqi) capped = true;
-                // bisection to full accuracy, then one more Getvec
-                for (int k = 0; k < 2100; ++k) {
-                    const double wd = h - l;
-                    if (!(wd > fmax(4.0 * kEps * fmax(fabs(l), fabs(h)), 4.0 * kSafmin))) break;
-                    const double mid = l + 0.5 * wd;
-                    if (!(mid > l && mid < h)) break;
-                    steps += n;
-                    if (negcount_ldl(n, d, dll, mid) < j) l = mid; else h = mid;
+                steps += (unsigned long long)(fend + 1);
+            } else if (!done && k == 1) {
+                double f = __ldg(d + n - 1) - lam, hh = 1.0;
+                int G = 0, sh = 0;
+                S.E(n - 1).y = 0;
+                for (int i = n - 2; i >= blow; --i) {
+                    double hv = fma(__ldg(dll + i), hh, f);
+                    if (is_zero(hv)) hv = -hh * 0x1p-80;
+                    const int sgh = sign_bit(hv);
+                    cntb += sgh ^ sh;
+                    const double df = __ldg(d + i) * f;
+                    f = fma(-lam, hv, df);
+                    S.H(i) = hv;
+                    S.Q(i) = df;
+                    S.E(i).y = G;
+                    G -= rescale2(hv, f);
+                    hh = hv;
+                    sh = sgh;
                 }
-                lam = l + 0.5 * (h - l);
-                r = -1;
-                fb = true;
+                steps += (unsigned long long)(n - 1 - blow);
             }
-            // Normalise (largest entry positive) and return the Rayleigh quotient of z with
-            // respect to the input T (accuracy remark 5 of Sec. 3.1.2): it removes the bias
-            // of the root's random perturbation and minimises ||T z - w z||.
+            __syncwarp();
+            cntf = __shfl_sync(FULL_MASK, cntf, tbase);
+            cntb = __shfl_sync(FULL_MASK, cntb, tbase + 1);
+            c_last = __shfl_sync(FULL_MASK, c_last, tbase);
+            cprev_last = __shfl_sync(FULL_MASK, cprev_last, tbase);
+            // ---- pass 2: twist index (full factorizations)
+            float best = 3.0e38f;
+            int rr = n - 1;
+            if (!done && full) {
+                if (k == 0) {
+                    best = log2abs(c_last) - log2abs(cprev_last);
+                    if (!(best == best)) best = 3.0e38f;
+                }
+                for (int i = k; i < n - 1; i += kTeam) {
+                    const double ci = S.C(i), hv = S.H(i);
+                    const double num = fma(S.A(i), hv, ci * S.Q(i));
+                    const float key = log2abs(num) - log2abs(ci * hv);
+                    if (key < best || (key == best && i < rr)) { best = key; rr = i; }
+                }
+            }
+            team_argmin(best, rr);
+            double gamma = 1.0;
+            int negc = 0;
+            if (!done) {
+                if (full) r = rr;
+                double gnum, gden;
+                if (r == n - 1) {
+                    gnum = c_last;
+                    gden = cprev_last;
+                } else {
+                    const double ci = S.C(r), hv = S.H(r);
+                    gnum = fma(S.A(r), hv, ci * S.Q(r));
+                    gden = ci * hv;
+                }
+                gamma = gnum / gden;
+                negc = full ? cntf : cntf + cntb + sign_bit(gamma);
+            }
+            // ---- pass 3: solve (z_r = 1), each lane on every kTeam-th element
+            double ss = 0.0;
+            long long zb = 0;
+            int zi_max = 0x7fffffff;
+            if (!done) {
+                const int rf = S.E(r).x;
+                const double icr = 1.0 / S.C(r);
+                const double ihr = (r < n - 1) ? 1.0 / S.H(r) : 1.0;
+                const int rg = (r < n - 1) ? S.E(r).y : 0;
+                const double qmr = Qm[r], iqmr = iQm[r];
+                const int qer = Qe[r];
+                for (int i = k; i < n; i += kTeam) {
+                    double z;
+                    if (i < r) {
+                        z = scale2(qmr * iQm[i] * S.C(i) * icr, qer - Qe[i] + S.E(i).x - rf);
+                    } else if (i > r) {
+                        const double hv = (i < n - 1) ? S.H(i) : 1.0;
+                        const int gi = (i < n - 1) ? S.E(i).y : 0;
+                        z = scale2(Qm[i] * iqmr * hv * ihr, Qe[i] - qer + gi - rg);
+                    } else {
+                        z = 1.0;
+                    }
+                    zc[i] = z;
+                    ss = fma(z, z, ss);
+                    const long long b = __double_as_longlong(z) & 0x7fffffffffffffffll;
+                    if (b > zb) { zb = b; zi_max = i; }
+                }
+                steps += (unsigned long long)((n + kTeam - 1) / kTeam);
+            }
+            ss = team_sum(ss);
+            team_argmax_bits(zb, zi_max);
+            if (done) continue;
+            // ---- acceptance (uniform within the team)
+            nrm2 = ss;
+            imax = zi_max;
+            ++it_n;
+            if (negc >= j) h = fmin(h, lam); else l = fmax(l, lam);
+            const double resid = fabs(gamma) / sqrt(nrm2);
+            rqc = gamma / nrm2;
+            const bool conv = (resid < tol1 * gap) || (fabs(rqc) < tol2 * fabs(lam));
+            // RQI converges cubically; a correction that no longer shrinks (at least by
+            // half) while tiny against the gap sits at the representation's noise level
+            const bool stalled = it_n >= 2 && fabs(rqc) >= 0.5 * prev_arqc && fabs(rqc) <= 1e-3 * gap;
+            const bool nofault = !(fault_mask & MR3_FAULT_RQI_NOCONV);
+            if (fb || ((conv || stalled) && nofault)) { done = true; continue; }
+            prev_arqc = fabs(rqc);
+            const bool sign_ok = (negc < j) ? (rqc > 0.0) : (rqc < 0.0);
+            const double lnew = lam + rqc;
+            if (it_n < max_rqi && sign_ok && lnew >= l && lnew <= h) {
+                lam = lnew;
+                continue;
+            }
+            // a correction at the rounding noise of the factorization cannot improve lam
+            if (nofault && fabs(rqc) <= tol_noise * fabs(lam)) { done = true; continue; }
+            if (it_n >= max_rqi) capped = true;
+            // bisection to full accuracy (every lane of the team, identically), then one
+            // more Getvec
+            for (int kk = 0; kk < 2100; ++kk) {
+                const double wd = h - l;
+                if (!(wd > fmax(4.0 * kEps * fmax(fabs(l), fabs(h)), 4.0 * kSafmin))) break;
+                const double mid = l + 0.5 * wd;
+                if (!(mid > l && mid < h)) break;
+                if (k == 0) steps += n;
+                if (negcount_ldl(n, d, dll, mid) < j) l = mid; else h = mid;
+            }
+            lam = l + 0.5 * (h - l);
+            r = -1;
+            fb = true;
+        }
+        // ---- normalise (an entry of largest magnitude positive) and the Rayleigh quotient
+        double rq = 0.0;
+        if (active) {
             const double zsign = (zc[imax] < 0.0) ? -1.0 : 1.0;
             const double scale = zsign / sqrt(nrm2);
-            const double *td = Din + B.off, *te = Ein + B.off;
-            double rq = 0.0, zprev = 0.0;
-            for (int i = 0; i < n; ++i) {
-                const double zi = zc[i] * scale;
-                zc[i] = zi;
+            for (int i = k; i < n; i += kTeam) zc[i] *= scale;
+        }
+        __syncwarp();
+        if (active) {
+            for (int i = k; i < n; i += kTeam) {
+                const double zi = zc[i];
                 rq = fma(__ldg(td + i) * zi, zi, rq);
-                if (i > 0) rq = fma(2.0 * __ldg(te + i - 1) * zprev, zi, rq);
-                zprev = zi;
+                if (i + 1 < n) rq = fma(2.0 * __ldg(te + i) * zi, zc[i + 1], rq);
             }
+        }
+        rq = team_sum(rq);
+        if (active && k == 0) {
             w[c] = rq;
             iters += it_n;
             itmax = max(itmax, it_n);
             nfb += fb ? 1 : 0;
             ncap += capped ? 1 : 0;
         }
+        (void)sigma;
+        __syncwarp();
     }
     for (int o = 16; o > 0; o >>= 1) {
         steps += __shfl_xor_sync(FULL_MASK, steps, o);
@@ -343,8 +371,6 @@ __global__ void __launch_bounds__(32) k_rqi(int nsingle, const SingleItem *__res
     }
 }
 
-// One warp per block so that the warps spread over all SMs (each SM has only two FP64
-// FMA lanes per clock); with few singletons a warp takes 8 or 16 of them instead of 32.
 void launch_rqi(int nsingle, const SingleItem *singles, const Node *nodes, const BlkDesc *blks,
                 const MatDesc *mats, const double *pool, const int *jloc, const double *lo,
                 const double *hi, const double *gapl, const double *gapr, const double *d,
@@ -352,14 +378,15 @@ void launch_rqi(int nsingle, const SingleItem *singles, const Node *nodes, const
                 int max_rqi, unsigned fault_mask, int *work_counter, DevInfo *info,
                 cudaStream_t s) {
     if (nsingle <= 0) return;
-    int lanes = 32;
-    while (lanes > 8 && (long long)nsingle < (long long)lanes * 2 * 152) lanes >>= 1;
-    const int want = (nsingle + lanes - 1) / lanes;
+    const int want = (nsingle + kTeams - 1) / kTeams;
     const int nblocks = want < nslots ? want : nslots;
     cudaMemsetAsync(work_counter, 0, sizeof(int), s);
     k_rqi<<<nblocks, 32, 0, s>>>(nsingle, singles, nodes, blks, mats, pool, jloc, lo, hi, gapl,
                                  gapr, d, e, w, Z, scratch, nmax, max_rqi, fault_mask,
-                                 work_counter, lanes, info);
+                                 work_counter, info);
 }
+
+int rqi_scratch_per_index() { return kScratchPerIndex; }
+int rqi_singles_per_slot() { return kTeams; }
 
 } // namespace mr3

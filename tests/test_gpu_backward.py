@@ -77,13 +77,23 @@ def test_matches_dense_eigh_autograd(cuda, n):
     assert np.max(np.abs(de - et.grad.numpy())) <= 1e-8 * scale
 
 
+def _separated(n, seed):
+    """Tridiagonal with well-separated eigenvalues (diagonal i + U(-0.1, 0.1), off-diagonal
+    U(-0.3, 0.3)): central differences of eigenvalues have truncation error ~(h/gap)^2, and
+    random tridiagonals have near-crossings (Poisson-like level statistics)."""
+    d = np.arange(n, dtype=np.float64) + 0.1 * tm.uniform(seed, n)
+    e = 0.3 * tm.uniform(seed + 1, n - 1)
+    return d, e
+
+
 @pytest.mark.parametrize("n", [64, 512])
 def test_central_finite_differences_eigenvalue_part(cuda, n):
     # eigenvalues are determined to ~n eps ||T||, so central differences at h = 1e-6 of
-    # sum(g . lambda) resolve the gradient to ~1e-8 relative
-    d, e = tm.random_uniform(n, 41, 42)
+    # sum(g . lambda) resolve the gradient to ~1e-8 relative when the gaps are O(1)
+    d, e = _separated(n, 41)
     g = tm.normal(43, n)
     w, Z = _fwd(d, e)
+    assert np.diff(w.cpu().numpy()).min() > 0.1
     dd, de = _bwd(w, Z, g=g)
 
     def loss(dv, ev):
