@@ -176,52 +176,42 @@ __global__ void __launch_bounds__(32) k_rqi(int nsingle, const SingleItem *__res
             const bool need_last = full || r == n - 1;
             const int fend = full ? n - 1 : r;
             const int blow = full ? 0 : r;
-            // ---- pass 1: lane 0 forward recurrence, lane 1 backward recurrence
+            // ---- pass 1: lanes 0 and 1 run the forward and the backward recurrence in one
+            // instruction stream.  Both read X' = p X + Y, Y' = q Y - lam X' with
+            //   forward  (lane 0): X = c, Y = a, (p, q) = (d_i, dll_i), i = t upward;
+            //   backward (lane 1): X = h, Y = f, (p, q) = (dll_i, d_i), i = n-2-t downward.
             int cntf = 0, cntb = 0;
             double c_last = 1.0, cprev_last = 1.0;
-            if (!done && k == 0) {
-                double a = -lam, cp = 1.0;
-                int F = 0, sp = 0;
-                for (int i = 0; i <= fend; ++i) {
-                    S.A(i) = a;
-                    S.C(i) = cp;
-                    S.E(i).x = F;
-                    if (i == fend && !need_last) break;
-                    double cc = fma(__ldg(d + i), cp, a);
-                    if (is_zero(cc)) cc = -cp * 0x1p-80;
-                    const int sc = sign_bit(cc);
-                    if (full || i < r) cntf += sc ^ sp;
-                    if (i == n - 1) {
-                        c_last = cc;
-                        cprev_last = cp;
-                        break;
-                    }
-                    const double tt = __ldg(dll + i) * a;
-                    a = fma(-lam, cc, tt);
-                    F -= rescale2(cc, a);
-                    cp = cc;
+            if (!done && k < 2) {
+                const bool bw = (k == 1);
+                // steps: forward indices 0..fend (the step at fend only stores unless c_{n-1}
+                // is needed), backward indices n-2 .. blow
+                const int nsteps = bw ? (n - 1 - blow) : (fend + 1);
+                const double *P = bw ? dll : d;
+                const double *Qv = bw ? d : dll;
+                double X = 1.0, Y = bw ? (__ldg(d + n - 1) - lam) : -lam;
+                int Sx = 0, sp = 0, cnt = 0;
+                if (bw) S.E(n - 1).y = 0;
+                for (int t = 0; t < nsteps; ++t) {
+                    const int i = bw ? (n - 2 - t) : t;
+                    const double pi = __ldg(P + i);
+                    const double qi = (i < n - 1) ? __ldg(Qv + i) : 0.0;
+                    if (!bw) { S.A(i) = Y; S.C(i) = X; S.E(i).x = Sx; }
+                    if (!bw && i == fend && !need_last) break;
+                    double Xn = fma(pi, X, Y);
+                    if (is_zero(Xn)) Xn = -X * 0x1p-80;
+                    const int sc = sign_bit(Xn);
+                    if (bw || full || i < r) cnt += sc ^ sp;
+                    if (!bw && i == n - 1) { c_last = Xn; cprev_last = X; break; }
+                    const double qY = qi * Y;
+                    Y = fma(-lam, Xn, qY);
+                    if (bw) { S.H(i) = Xn; S.Q(i) = qY; S.E(i).y = Sx; }
+                    Sx -= rescale2(Xn, Y);
+                    X = Xn;
                     sp = sc;
                 }
-                steps += (unsigned long long)(fend + 1);
-            } else if (!done && k == 1) {
-                double f = __ldg(d + n - 1) - lam, hh = 1.0;
-                int G = 0, sh = 0;
-                S.E(n - 1).y = 0;
-                for (int i = n - 2; i >= blow; --i) {
-                    double hv = fma(__ldg(dll + i), hh, f);
-                    if (is_zero(hv)) hv = -hh * 0x1p-80;
-                    const int sgh = sign_bit(hv);
-                    cntb += sgh ^ sh;
-                    const double df = __ldg(d + i) * f;
-                    f = fma(-lam, hv, df);
-                    S.H(i) = hv;
-                    S.Q(i) = df;
-                    S.E(i).y = G;
-                    G -= rescale2(hv, f);
-                    hh = hv;
-                    sh = sgh;
-                }
-                steps += (unsigned long long)(n - 1 - blow);
+                if (bw) cntb = cnt; else cntf = cnt;
+                steps += (unsigned long long)nsteps;
             }
             __syncwarp();
             cntf = __shfl_sync(FULL_MASK, cntf, tbase);

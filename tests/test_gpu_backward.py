@@ -78,11 +78,12 @@ def test_matches_dense_eigh_autograd(cuda, n):
 
 
 def _separated(n, seed):
-    """Tridiagonal with well-separated eigenvalues (diagonal i + U(-0.1, 0.1), off-diagonal
-    U(-0.3, 0.3)): central differences of eigenvalues have truncation error ~(h/gap)^2, and
+    """Tridiagonal with well-separated eigenvalues ((i + U(-0.1, 0.1)) / n on the diagonal,
+    U(-0.3, 0.3) / n off it, so ||T|| ~ 1 and gaps ~ 1/n): central differences of
+    eigenvalues have truncation error ~(h/gap)^2 and rounding noise ~eps ||T|| / h, while
     random tridiagonals have near-crossings (Poisson-like level statistics)."""
-    d = np.arange(n, dtype=np.float64) + 0.1 * tm.uniform(seed, n)
-    e = 0.3 * tm.uniform(seed + 1, n - 1)
+    d = (np.arange(n, dtype=np.float64) + 0.1 * tm.uniform(seed, n)) / n
+    e = 0.3 * tm.uniform(seed + 1, n - 1) / n
     return d, e
 
 
@@ -93,7 +94,7 @@ def test_central_finite_differences_eigenvalue_part(cuda, n):
     d, e = _separated(n, 41)
     g = tm.normal(43, n)
     w, Z = _fwd(d, e)
-    assert np.diff(w.cpu().numpy()).min() > 0.1
+    assert np.diff(w.cpu().numpy()).min() > 0.1 / n
     dd, de = _bwd(w, Z, g=g)
 
     def loss(dv, ev):
