@@ -330,10 +330,11 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
         int *next_active = ws.get<int>(hc.nactive);
         CKW(ws);
         tk = prof.begin();
+        launch_refine_ends(hc.ncluster, clusters, cur_nodes, blks, cur_pool, jloc, lo, hi, dinfo, s);
         launch_shift(hc.ncluster, clusters, crep, cur_nodes, blks, cur_pool, next_pool,
                      next_nodes, tau, cnode, next_active, jloc, lo, hi, o.max_tries, o.fault_mask,
                      dinfo, s);
-        prof.end(tk, 5, 1);
+        prof.end(tk, 5, 2);
         tk = prof.begin();
         launch_bisect(hc.nactive, next_active, lanes_for(hc.nactive, o), (int)ncols, cnode,
                       next_nodes, blks, next_pool, jloc, lo, hi, rtol, tau, dinfo, s);

@@ -81,8 +81,10 @@ __device__ __forceinline__ int negcount_df(int n, const float4 *__restrict__ dd,
     const dfloat ns = df_neg(sigma);
     dfloat a = ns, cp = {1.f, 0.f};
     int sp = 0, cnt = 0;
+    float4 qn = __ldg(dd); // prefetched data of step i
     for (int i = 0; i < n; ++i) {
-        const float4 q = __ldg(dd + i);
+        const float4 q = qn;
+        if (i + 1 < n) qn = __ldg(dd + i + 1);
         const dfloat di = {q.x, q.y};
         dfloat c = df_add(df_mul(di, cp), a);
         if (c.h == 0.f) { c.h = -cp.h * 0x1p-30f; c.l = 0.f; }

@@ -153,9 +153,13 @@ __device__ __forceinline__ int negcount_ldl(int n, const double *__restrict__ d,
                                             const double *__restrict__ dll, double sigma) {
     double a = -sigma, cp = 1.0;
     int sp = 0, cnt = 0;
+    double dn = __ldg(d), ln = (n > 1) ? __ldg(dll) : 0.0; // prefetched data of step i
     for (int i = 0; i < n - 1; ++i) {
-        const double t = __ldg(dll + i) * a;
-        double c = fma(__ldg(d + i), cp, a);
+        const double di = dn, li = ln;
+        dn = __ldg(d + i + 1);
+        ln = (i + 1 < n - 1) ? __ldg(dll + i + 1) : 0.0;
+        const double t = li * a;
+        double c = fma(di, cp, a);
         if (is_zero(c)) c = -cp * 0x1p-80;
         const int sc = sign_bit(c);
         cnt += sc ^ sp;
@@ -169,7 +173,7 @@ __device__ __forceinline__ int negcount_ldl(int n, const double *__restrict__ d,
         cp = c;
         sp = sc;
     }
-    double c = fma(__ldg(d + n - 1), cp, a);
+    double c = fma(dn, cp, a);
     int sc = is_zero(c) ? (sp ^ 1) : sign_bit(c);
     cnt += sc ^ sp;
     return cnt;

@@ -53,6 +53,10 @@ void launch_classify(int nnode, const Node *nodes, const BlkDesc *blks, const do
                      const double *hi, double gaptol, double *gapl, double *gapr,
                      SingleItem *singles, ClusterItem *clusters, long long *cluster_rep,
                      int *cnode, LevelCounters *ctr, DevInfo *info, cudaStream_t s);
+// Refine the two extreme eigenvalues of every cluster (Alg. "Shifting the spectrum" line 1).
+void launch_refine_ends(int ncluster, const ClusterItem *clusters, const Node *nodes,
+                        const BlkDesc *blks, const double *pool, const int *jloc, double *lo,
+                        double *hi, DevInfo *info, cudaStream_t s);
 void launch_shift(int ncluster, const ClusterItem *clusters, const long long *cluster_rep,
                   const Node *nodes, const BlkDesc *blks, const double *pool, double *childpool,
                   Node *child_nodes, double *child_tau, int *cnode, int *active_list,

@@ -366,6 +366,96 @@ void launch_classify(int nnode, const Node *nodes, const BlkDesc *blks, const do
                                                             cluster_rep, cnode, ctr, info);
 }
 
+// ------------------------------------------------------------------ cluster ends
+
+// Alg. "Shifting the spectrum" line 1: refine the extreme eigenvalues of every cluster
+// before the shift.  A group of E lanes owns one end (group 2c: lambda_p, group 2c+1:
+// lambda_q of cluster c) and multisects it until the interval is below 1e-3 of a lower
+// bound on the gap to the inner neighbour (so that a shift just outside the interval
+// leaves that end well separated in the child) or at full accuracy (4 eps |lambda|).  The
+// bound starts from the neighbour's interval and tightens with every sample whose count
+// shows the neighbour on its far side.  Counts are double-float while the interval is
+// wider than 1e-11 relative, binary64 below.
+__global__ void k_refine_ends(int ncluster, const ClusterItem *__restrict__ clusters,
+                              const Node *__restrict__ nodes, const BlkDesc *__restrict__ blks,
+                              const double *__restrict__ pool, const int *__restrict__ jloc,
+                              double *lo, double *hi, int E, DevInfo *info) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int g = tid / E, k = lane % E, gbase = lane - k;
+    const unsigned gmask = (E == 32) ? 0xffffffffu : (((1u << E) - 1u) << gbase);
+    const bool active = g < 2 * ncluster;
+    const int side = g & 1;
+    int n = 1, tgt = 1, col = 0;
+    Node P;
+    P.dfok = 0;
+    const double *pd = pool;
+    double L = 0.0, H = 0.0, nb = 0.0;
+    if (active) {
+        const ClusterItem C = clusters[g >> 1];
+        P = nodes[C.node];
+        n = blks[P.blk].n;
+        pd = pool + P.rep;
+        col = side ? C.c1 : C.c0;
+        tgt = jloc[col];
+        L = lo[col];
+        H = hi[col];
+        nb = side ? hi[col - 1] : lo[col + 1];
+    }
+    unsigned long long steps = 0;
+    for (int sweep = 0; sweep < 64; ++sweep) {
+        const double w = H - L;
+        const double gap_lb = side ? (L - nb) : (nb - H);
+        const double tol = fmax(4.0 * kEps * fmax(fabs(L), fabs(H)), 1e-3 * fmax(gap_lb, 0.0));
+        bool done = !active || !(w > tol);
+        const double x = L + (k + 1) * (w / (E + 1));
+        if (__ballot_sync(0xffffffffu, !(x > L && x < H)) & gmask) done = true;
+        if (__all_sync(0xffffffffu, done)) break;
+        int cnt = 0;
+        if (!done) {
+            cnt = (w > 1e-11 * fmax(fabs(L), fabs(H))) ? node_count(P, n, pd, x)
+                                                        : negcount_ldl(n, pd, pd + 2 * n, x);
+            steps += n;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, cnt < tgt);
+        const int t = __popc(bal & gmask);
+        const double xl = __shfl_sync(0xffffffffu, x, gbase + (t > 0 ? t - 1 : 0));
+        const double xh = __shfl_sync(0xffffffffu, x, gbase + (t < E ? t : E - 1));
+        // left end: count <= j gives lambda_{j+1} >= x (largest such x); right end:
+        // count >= j - 1 gives lambda_{j-1} < x (smallest such x)
+        const bool nbl = side ? (cnt >= tgt - 1) : (cnt <= tgt);
+        const unsigned hb = (__ballot_sync(0xffffffffu, nbl && !done) & gmask) >> gbase;
+        const int first = hb ? __ffs(hb) - 1 : 0, last = hb ? 31 - __clz(hb) : 0;
+        const double xf = __shfl_sync(0xffffffffu, x, gbase + first);
+        const double xlst = __shfl_sync(0xffffffffu, x, gbase + last);
+        if (!done) {
+            if (hb) nb = side ? fmin(nb, xf) : fmax(nb, xlst);
+            if (t > 0) L = xl;
+            if (t < E) H = xh;
+        }
+    }
+    if (active && k == 0) {
+        lo[col] = L;
+        hi[col] = H;
+    }
+    for (int o = 16; o > 0; o >>= 1) steps += __shfl_xor_sync(0xffffffffu, steps, o);
+    if (lane == 0 && steps) atomicAdd(&info->shift_steps, steps);
+}
+
+void launch_refine_ends(int ncluster, const ClusterItem *clusters, const Node *nodes,
+                        const BlkDesc *blks, const double *pool, const int *jloc, double *lo,
+                        double *hi, DevInfo *info, cudaStream_t s) {
+    if (ncluster <= 0) return;
+    // lanes per end: many ends -> fewer lanes (throughput), few ends -> more (latency)
+    const long long ends = 2ll * ncluster;
+    int E = 4;
+    while (E < 32 && ends * (2 * E) <= 152ll * 32 * 8) E *= 2;
+    const long long threads = ends * E;
+    const int bs = 64;
+    k_refine_ends<<<(unsigned)((threads + bs - 1) / bs), bs, 0, s>>>(ncluster, clusters, nodes, blks,
+                                                                     pool, jloc, lo, hi, E, info);
+}
+
 // ------------------------------------------------------------------ cluster shift
 
 // Trial dstqds L+ D+ L+^T = L D L^T - tau I in homogeneous form (see negcount_ldl).
@@ -409,9 +499,7 @@ __device__ void trial_shift(int n, const double *__restrict__ d, const double *_
 }
 
 // One warp per cluster {p..q} of node P (Alg. "Shifting the spectrum" inside a C-task).
-//  1. Refine the cluster's extreme eigenvalues (lanes 0-15: lambda_p, lanes 16-31:
-//     lambda_q) by 16-point multisection until the interval is below 1e-3 of a lower
-//     bound of the gap to the inner neighbour, or at full accuracy (4 eps |lambda|).
+//  1. The cluster's extreme eigenvalues come refined from k_refine_ends.
 //  2. Candidates tau_l = lo_p - 100 eps |lo_p| and tau_r = hi_q + 100 eps |hi_q| (lanes 0, 1);
 //     a candidate exists when its factorization has no zero pivot and stays finite; of
 //     existing ones the smaller growth max|d+_i| is taken; it is accepted when
@@ -439,48 +527,10 @@ __global__ void k_shift(int ncluster, const ClusterItem *__restrict__ clusters,
     const int p = C.c0, q = C.c1;
     unsigned long long steps = 0;
 
-    // ---- 1. refine the cluster ends
-    const int half = lane >> 4, k = lane & 15;
-    const int tgt = half ? jloc[q] : jloc[p];
-    double L = half ? lo[q] : lo[p];
-    double H = half ? hi[q] : hi[p];
-    double nb = half ? hi[q - 1] : lo[p + 1]; // bound on the inner neighbour
-    for (int sweep = 0; sweep < 16; ++sweep) {
-        const double w = H - L;
-        const double gap_lb = half ? (L - nb) : (nb - H);
-        const double tol = fmax(4.0 * kEps * fmax(fabs(L), fabs(H)), 1e-3 * fmax(gap_lb, 0.0));
-        const bool done = !(w > tol);
-        const unsigned dm = __ballot_sync(FULL_MASK, done);
-        if ((dm & 0x00010001u) == 0x00010001u) break;
-        const double x = L + (k + 1) * (w / 17.0);
-        int cnt = 0;
-        if (!done) {
-            cnt = (w > 1e-11 * fmax(fabs(L), fabs(H))) ? node_count(P, n, pd, x)
-                                                        : negcount_ldl(n, pd, pdll, x);
-            steps += n;
-        }
-        const unsigned bal = __ballot_sync(FULL_MASK, cnt < tgt);
-        const int t = __popc((bal >> (16 * half)) & 0xffffu);
-        const double xl = __shfl_sync(FULL_MASK, x, 16 * half + (t > 0 ? t - 1 : 0));
-        const double xh = __shfl_sync(FULL_MASK, x, 16 * half + (t < 16 ? t : 15));
-        // samples that bound the inner neighbour: left end, count <= j_p gives
-        // lambda_{p+1} >= x (take the largest); right end, count >= j_q - 1 gives
-        // lambda_{q-1} < x (take the smallest)
-        const bool nbl = half ? (cnt >= tgt - 1) : (cnt <= tgt);
-        const unsigned hb = (__ballot_sync(FULL_MASK, nbl) >> (16 * half)) & 0xffffu;
-        const int first = hb ? __ffs(hb) - 1 : 0, last = hb ? 31 - __clz(hb) : 0;
-        const double xf = __shfl_sync(FULL_MASK, x, 16 * half + first);
-        const double xlst = __shfl_sync(FULL_MASK, x, 16 * half + last);
-        if (!done) {
-            if (hb) nb = half ? fmin(nb, xf) : fmax(nb, xlst);
-            if (t > 0) L = xl;
-            if (t < 16) H = xh;
-        }
-    }
-    if (lane == 0) { lo[p] = L; hi[p] = H; }
-    if (lane == 16) { lo[q] = L; hi[q] = H; }
-    const double Lp = __shfl_sync(FULL_MASK, L, 0);
-    const double Hq = __shfl_sync(FULL_MASK, H, 16);
+    // ---- 1. the cluster ends were refined by k_refine_ends
+    const double L = lo[p], H = hi[q];
+    const double Lp = L;
+    const double Hq = H;
 
     // ---- 2. shift candidates
     const double tau_l0 = Lp - MR3_TAU_OFFSET * kEps * fabs(Lp);

@@ -192,23 +192,31 @@ __global__ void __launch_bounds__(32) k_rqi(int nsingle, const SingleItem *__res
                 double X = 1.0, Y = bw ? (__ldg(d + n - 1) - lam) : -lam;
                 int Sx = 0, sp = 0, cnt = 0;
                 if (bw) S.E(n - 1).y = 0;
-                for (int t = 0; t < nsteps; ++t) {
-                    const int i = bw ? (n - 2 - t) : t;
-                    const double pi = __ldg(P + i);
-                    const double qi = (i < n - 1) ? __ldg(Qv + i) : 0.0;
+                // data of step t + 1 is loaded while step t runs (software prefetch)
+                int i = bw ? (n - 2) : 0;
+                const int di = bw ? -1 : 1;
+                double pi = (nsteps > 0) ? __ldg(P + i) : 0.0;
+                double qi = (nsteps > 0 && i < n - 1) ? __ldg(Qv + i) : 0.0;
+                for (int t = 0; t < nsteps; ++t, i += di) {
+                    const int inext = i + di;
+                    const bool more = t + 1 < nsteps;
+                    const double pn = more ? __ldg(P + inext) : 0.0;
+                    const double qn = (more && inext < n - 1) ? __ldg(Qv + inext) : 0.0;
                     if (!bw) { S.A(i) = Y; S.C(i) = X; S.E(i).x = Sx; }
                     if (!bw && i == fend && !need_last) break;
+                    const double qY = qi * Y;
                     double Xn = fma(pi, X, Y);
                     if (is_zero(Xn)) Xn = -X * 0x1p-80;
                     const int sc = sign_bit(Xn);
                     if (bw || full || i < r) cnt += sc ^ sp;
                     if (!bw && i == n - 1) { c_last = Xn; cprev_last = X; break; }
-                    const double qY = qi * Y;
                     Y = fma(-lam, Xn, qY);
                     if (bw) { S.H(i) = Xn; S.Q(i) = qY; S.E(i).y = Sx; }
                     Sx -= rescale2(Xn, Y);
                     X = Xn;
                     sp = sc;
+                    pi = pn;
+                    qi = qn;
                 }
                 if (bw) cntb = cnt; else cntf = cnt;
                 steps += (unsigned long long)nsteps;

@@ -78,12 +78,12 @@ def test_matches_dense_eigh_autograd(cuda, n):
 
 
 def _separated(n, seed):
-    """Tridiagonal with well-separated eigenvalues ((i + U(-0.1, 0.1)) / n on the diagonal,
-    U(-0.3, 0.3) / n off it, so ||T|| ~ 1 and gaps ~ 1/n): central differences of
+    """Tridiagonal with well-separated eigenvalues (8 (i + U(-0.1, 0.1)) / n on the diagonal,
+    2.4 U(-1, 1) / n off it, so ||T|| ~ 8 and gaps ~ 6/n): central differences of
     eigenvalues have truncation error ~(h/gap)^2 and rounding noise ~eps ||T|| / h, while
     random tridiagonals have near-crossings (Poisson-like level statistics)."""
-    d = (np.arange(n, dtype=np.float64) + 0.1 * tm.uniform(seed, n)) / n
-    e = 0.3 * tm.uniform(seed + 1, n - 1) / n
+    d = 8.0 * (np.arange(n, dtype=np.float64) + 0.1 * tm.uniform(seed, n)) / n
+    e = 2.4 * tm.uniform(seed + 1, n - 1) / n
     return d, e
 
 
@@ -94,7 +94,7 @@ def test_central_finite_differences_eigenvalue_part(cuda, n):
     d, e = _separated(n, 41)
     g = tm.normal(43, n)
     w, Z = _fwd(d, e)
-    assert np.diff(w.cpu().numpy()).min() > 0.1 / n
+    assert np.diff(w.cpu().numpy()).min() > 1.0 / n
     dd, de = _bwd(w, Z, g=g)
 
     def loss(dv, ev):
@@ -103,8 +103,11 @@ def test_central_finite_differences_eigenvalue_part(cuda, n):
 
     h = 1e-6
     for k in range(3):
+        # unit direction, so that the perturbation h V of T has norm ~h
         vd = tm.normal(500 + 2 * k, n)
         ve = tm.normal(501 + 2 * k, n - 1)
+        nv = np.sqrt(vd @ vd + 2 * ve @ ve)
+        vd, ve = vd / nv, ve / nv
         fd = (loss(d + h * vd, e + h * ve) - loss(d - h * vd, e - h * ve)) / (2 * h)
         an = float(dd @ vd + de @ ve)
         assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)
