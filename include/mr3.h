@@ -189,6 +189,29 @@ int mr3_backward(int n, int k, const double *w, const double *Z, int ldz, const 
                  const double *gZ, int ldgz, double *dd, double *de, const mr3_opts *opts,
                  void *stream);
 
+/*
+ * mr3_stemr_static -- mr3_stemr for one matrix of order n <= MR3_STATIC_MAX_N, with all
+ * device workspace inside a fixed array of MR3_STATIC_SCRATCH_BYTES that the library
+ * holds on each device: the call allocates no device memory.  The thesis has no
+ * counterpart; this entry point exists for callers that cannot let a library allocate
+ * (their device memory is claimed in full up front, or no allocator may be entered).
+ *
+ *  Arguments, outputs, defaults and return codes as for mr3_stemr; opts->profile is
+ *  ignored (kernel_ms and kernel_launches stay zero).  Every step runs on `stream`.
+ *  Extra return code: MR3_ENOSCRATCH when n > MR3_STATIC_MAX_N (checked before any
+ *  device work), or when the representation tree of this matrix needs more room than
+ *  the array has (then w and Z are undefined, *m = 0, and the stream is idle on return).
+ *  Set-up: the first call made with a device current looks up that device's array and
+ *  caches its address; make that first call before beginning any stream capture.
+ *  Sharing: one array per device.  Calls that overlap in time on the same device (other
+ *  host threads, or streams not ordered with respect to each other) race on it: order them.
+ */
+#define MR3_STATIC_SCRATCH_BYTES (32u << 20) /* 32 MiB per device                 */
+#define MR3_STATIC_MAX_N 1024                /* largest order mr3_stemr_static takes */
+int mr3_stemr_static(int n, const double *d, const double *e, int range, double vl, double vu,
+                     int il, int iu, int *m, double *w, double *Z, int ldz,
+                     const mr3_opts *opts, mr3_info *info, void *stream);
+
 /* Message for a return code (static string). */
 const char *mr3_strerror(int code);
 

@@ -72,6 +72,8 @@ def lib():
                                     ctypes.POINTER(c_int), dp, dp, c_int,
                                     ctypes.POINTER(Opts), ctypes.POINTER(Info), vp]
             L.mr3_stemr.restype = c_int
+            L.mr3_stemr_static.argtypes = L.mr3_stemr.argtypes
+            L.mr3_stemr_static.restype = c_int
             L.mr3_stemr_host.argtypes = L.mr3_stemr.argtypes
             L.mr3_stemr_host.restype = c_int
             L.mr3_stemr_batched.argtypes = [c_int, vp, dp, dp, c_int, vp, vp, vp, vp, vp, dp,
@@ -163,6 +165,44 @@ def stemr(d, e, rng="A", vl=0.0, vu=0.0, il=1, iu=None, opts=None, stream=None):
     out = info.as_dict()
     out["status"] = rc
     return w[:k], Zb[:k].T, out
+
+
+def stemr_static(d, e, rng="A", vl=0.0, vu=0.0, il=1, iu=None, opts=None, stream=None,
+                 out=None):
+    """mr3_stemr_static: as stemr, for n <= STATIC_MAX_N, with the library's workspace in
+    a fixed per-device array (the call allocates no device memory).  `out` = (w, Zbuf)
+    lets the caller pass preallocated outputs: w float64 of >= n entries and Zbuf
+    float64 of shape (>= n, n), row j of Zbuf receiving eigenvector j."""
+    torch = _torch()
+    n = int(d.shape[0])
+    assert d.dtype == torch.float64 and d.is_cuda and d.is_contiguous()
+    if n > 1:
+        assert e.dtype == torch.float64 and e.is_cuda and e.is_contiguous() and e.shape[0] >= n - 1
+    r, vl, vu, il, iu, mcap = _range_args(rng, n, vl, vu, il, iu)
+    if out is None:
+        w = torch.empty(max(mcap, 1), dtype=torch.float64, device=d.device)
+        Zb = torch.empty((max(mcap, 1), max(n, 1)), dtype=torch.float64, device=d.device)
+    else:
+        w, Zb = out
+        assert w.dtype == torch.float64 and w.is_cuda and w.numel() >= mcap
+        assert (Zb.dtype == torch.float64 and Zb.is_cuda and Zb.is_contiguous()
+                and Zb.shape[0] >= mcap and Zb.shape[1] == max(n, 1))
+    m = ctypes.c_int(0)
+    info = Info()
+    o = opts if opts is not None else make_opts()
+    rc = lib().mr3_stemr_static(n, ctypes.c_void_p(d.data_ptr()),
+                                ctypes.c_void_p(e.data_ptr() if n > 1 else 0), r, vl, vu, il,
+                                iu, ctypes.byref(m), ctypes.c_void_p(w.data_ptr()),
+                                ctypes.c_void_p(Zb.data_ptr()), max(n, 1), ctypes.byref(o),
+                                ctypes.byref(info), _stream_ptr(stream))
+    _check(rc, "mr3_stemr_static")
+    k = m.value
+    res = info.as_dict()
+    res["status"] = rc
+    return w[:k], Zb[:k].T, res
+
+
+STATIC_MAX_N = 1024  # MR3_STATIC_MAX_N in include/mr3.h
 
 
 def stemr_host(d, e, rng="A", vl=0.0, vu=0.0, il=1, iu=None, opts=None, stream=None):
