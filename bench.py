@@ -360,6 +360,37 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_backward(args):
+    """Backward vs forward at n = 4096 (uniform(-1,1) d and e, all eigenpairs): loss
+    sum(g . lambda) + sum(G o Z), g and G standard normal.  Prints one JSON line."""
+    import torch
+    import paper_1401_4950_gb300 as mr3
+    dev = torch.device("cuda", 0)
+    n = args.n_bwd
+    d, e = tm.random_uniform(n, 501, 502)
+    g = torch.tensor(tm.normal(503, n), device=dev)
+    G = torch.tensor(tm.normal(504, n * n).reshape(n, n), device=dev).t().contiguous().t()
+    dt, et = torch.tensor(d, device=dev), torch.tensor(e, device=dev)
+    for _ in range(2):
+        w, Z, _ = mr3.stemr(dt, et)
+        mr3.backward(w, Z, g, G)
+    torch.cuda.synchronize()
+    reps = max(1, args.steps)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        w, Z, _ = mr3.stemr(dt, et)
+    torch.cuda.synchronize()
+    tf = (time.perf_counter() - t0) / reps
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        dd, de = mr3.backward(w, Z, g, G)
+    torch.cuda.synchronize()
+    tb = (time.perf_counter() - t0) / reps
+    print(json.dumps({"metric": "backward / forward time (n=%d, all eigenpairs, FP64)" % n,
+                      "value": tb / tf, "unit": "ratio", "forward_ms": 1e3 * tf,
+                      "backward_ms": 1e3 * tb}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -372,6 +403,9 @@ def main():
     ap.add_argument("--batched", action="store_true",
                     help="time the batched workload (one call vs per-matrix calls) instead")
     ap.add_argument("--batch", type=int, default=4096)
+    ap.add_argument("--backward", action="store_true",
+                    help="time the backward pass against the forward instead")
+    ap.add_argument("--n-bwd", type=int, default=4096)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -380,6 +414,9 @@ def main():
         return
     if args.batched:
         run_batched(args)
+        return
+    if args.backward:
+        run_backward(args)
         return
     run_gpu(args, args.config, rank, world)
 

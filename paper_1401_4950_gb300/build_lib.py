@@ -32,6 +32,11 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libmr3")
 
 
+def _cuda_libdir(nvcc: str) -> str:
+    """lib64 of the toolkit that holds nvcc (cuBLAS is loaded from there)."""
+    return os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
+
+
 def _stale(target: str, deps) -> bool:
     if not os.path.exists(target):
         return True
@@ -69,7 +74,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + ".%d.tmp" % os.getpid()
-        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"])
+        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static", "-lcublas",
+             "-Xlinker", "-rpath," + _cuda_libdir(nvcc)])
         os.replace(tmp, LIB)
     return LIB
 

@@ -236,3 +236,51 @@ def test_autograd_function(cuda):
     (w.sum()).backward()
     assert torch.allclose(dt.grad, torch.ones_like(dt), atol=1e-12)
     assert torch.max(torch.abs(et.grad)).item() <= 1e-12
+
+
+def _vector_part_fp64(w, Z, G):
+    """dbar, ebar of the vector part in plain binary64 on the CPU (the formula written out:
+    B = F o (Z^T G), Y = Z B, dbar_j = sum_k Y_jk Z_jk, ebar_j = sum_k Y_jk Z_j+1,k +
+    Y_j+1,k Z_jk), with the regularised F and delta = n eps ||T|| of the library."""
+    n = len(w)
+    delta = n * 2.0 ** -53 * max(abs(w[0]), abs(w[-1]))
+    D = w[None, :] - w[:, None]
+    F = D / (D * D + delta * delta)
+    np.fill_diagonal(F, 0.0)
+    Y = Z @ (F * (Z.T @ G))
+    dd = np.einsum("jk,jk->j", Y, Z)
+    de = np.einsum("jk,jk->j", Y[:-1], Z[1:]) + np.einsum("jk,jk->j", Y[1:], Z[:-1])
+    return dd, de
+
+
+@pytest.mark.parametrize("n,kind", [(256, "random"), (700, "random"), (1500, "one_two_one"),
+                                    (4500, "random")])
+def test_split_product_backward_matches_fp64(cuda, n, kind):
+    # the vector part through the bf16 slice products (n >= 256; two contraction chunks
+    # at n = 4500) against the same formula in binary64
+    d, e = tm.make(kind, n, seed=91)
+    G = tm.normal(92, n * n).reshape(n, n)
+    w, Z = _fwd(d, e)
+    dd, de = _bwd(w, Z, g=None, G=G)
+    wc, Zc = w.cpu().numpy(), Z.cpu().numpy()
+    rd, re_ = _vector_part_fp64(wc, Zc, G)
+    scale = max(np.abs(rd).max(), np.abs(re_).max())
+    assert np.max(np.abs(dd - rd)) <= 1e-11 * scale, np.max(np.abs(dd - rd)) / scale
+    assert np.max(np.abs(de - re_)) <= 1e-11 * scale, np.max(np.abs(de - re_)) / scale
+
+
+def test_split_product_wide_dynamic_range(cuda):
+    # columns of G spanning 2^-300 .. 2^300 and entries 2^20 apart inside a column: the
+    # power-of-two scaling per line keeps the slices in range (no overflow, no flush to 0)
+    n = 512
+    d, e = tm.make("random", n, seed=93)
+    G = tm.normal(94, n * n).reshape(n, n)
+    G *= np.exp2(np.linspace(-300, 300, n))[None, :]
+    G[::7] *= 2.0 ** -20
+    w, Z = _fwd(d, e)
+    dd, de = _bwd(w, Z, g=None, G=G)
+    rd, re_ = _vector_part_fp64(w.cpu().numpy(), Z.cpu().numpy(), G)
+    scale = max(np.abs(rd).max(), np.abs(re_).max())
+    assert np.all(np.isfinite(dd)) and np.all(np.isfinite(de))
+    assert np.max(np.abs(dd - rd)) <= 1e-11 * scale
+    assert np.max(np.abs(de - re_)) <= 1e-11 * scale
