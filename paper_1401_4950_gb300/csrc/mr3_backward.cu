@@ -15,8 +15,9 @@
 // binary64 at about 1.2 TFLOP/s, so for n >= kOzakiMinN they are computed as exact sums of
 // bf16 tensor-core products (the error-free splitting of Ozaki, Ogita, Oishi and Rump,
 // Numer. Algorithms 59 (2012)): every row of the left factor and every column of the
-// right one is scaled by a power of two into (-1, 1) and cut into s slices of beta bits,
-// each an integer held exactly in bf16; a slice-by-slice product summed over a chunk of at
+// right one is scaled by a power of two into (-1, 1) and cut into s slices of beta bits
+// (consecutive bit fields of its fixed-point fraction), each an integer held exactly in
+// bf16; a slice-by-slice product summed over a chunk of at
 // most 2^(24 - 2 beta) terms is an integer below 2^24 and comes out of an FP32-accumulating
 // GEMM exactly; the slice products whose weight 2^(-beta (p + q)) is below 2^(-beta (s+1))
 // are dropped (their sum is below 2^-54 of the scale), and the rest is summed in binary64.
@@ -25,31 +26,11 @@
 #include <cstring>
 #include <mutex>
 #include <cublas_v2.h>
-#include <cuda_bf16.h>
 #include "mr3.h"
 #include "mr3_internal.cuh"
 
 namespace mr3 {
 namespace {
-
-// dbar_j = sum_i g_i z_ji^2 ; ebar_j = 2 sum_i g_i z_ji z_{j+1,i}  (one thread per row j,
-// columns visited in order so that a warp reads 32 consecutive rows of a column).
-__global__ void k_bwd_eigvals(int n, int k, const double *__restrict__ Z, int ldz,
-                              const double *__restrict__ gw, double *dd, double *de) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    double sd = 0.0, se = 0.0;
-    if (gw) {
-        for (int i = 0; i < k; ++i) {
-            const double g = __ldg(gw + i);
-            const double a = __ldg(Z + (size_t)i * ldz + j);
-            sd = fma(g * a, a, sd);
-            if (j < n - 1) se = fma(g * a, __ldg(Z + (size_t)i * ldz + j + 1), se);
-        }
-    }
-    dd[j] = sd;
-    if (j < n - 1) de[j] = 2.0 * se;
-}
 
 // C (m x n, column-major, ldc) = op(A) * B with op(A) = A^T (transA) or A; A, B
 // column-major.  64 x 64 tile per CTA, 256 threads with a 4 x 4 register tile each,
@@ -115,24 +96,6 @@ __global__ void k_apply_F(int n, const double *__restrict__ w, double delta, dou
     C[idx] = C[idx] * (D / (D * D + delta * delta));
 }
 
-// dbar_j += sum_b Y_jb Z_jb ; ebar_j += sum_b (Y_jb Z_{j+1,b} + Y_{j+1,b} Z_jb).
-__global__ void k_bwd_vec_reduce(int n, const double *__restrict__ Y, const double *__restrict__ Z,
-                                 int ldz, double *dd, double *de) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    double sd = 0.0, se = 0.0;
-    for (int b = 0; b < n; ++b) {
-        const double y = Y[(size_t)b * n + j], z = Z[(size_t)b * ldz + j];
-        sd = fma(y, z, sd);
-        if (j < n - 1) {
-            const double y1 = Y[(size_t)b * n + j + 1], z1 = Z[(size_t)b * ldz + j + 1];
-            se = fma(y, z1, fma(y1, z, se));
-        }
-    }
-    dd[j] += sd;
-    if (j < n - 1) de[j] += se;
-}
-
 // ---- Ozaki splitting
 
 constexpr int kOzakiMinN = 256;   // below this the binary64 tile GEMM is as fast
@@ -149,59 +112,104 @@ OzakiPlan ozaki_plan(int K) {
     p.chunk = std::min(K, kOzakiChunk);
     int lg = 0;
     while ((1 << lg) < p.chunk) ++lg;
-    // |slice 1| <= 2^beta, |slice p>1| <= 2^(beta-1): a chunk sum is at most 2^(2 beta + lg)
-    p.beta = std::min(8, (24 - lg) / 2); // bf16 holds integers up to 2^8 exactly
-    p.s = (54 + p.beta - 1) / p.beta;
+    // every slice is an integer of magnitude < 2^beta, so a chunk sum of slice products
+    // stays below 2^(2 beta + lg) <= 2^24; bf16 holds integers below 2^8 exactly
+    p.beta = std::min(8, (24 - lg) / 2);
+    p.s = (54 + p.beta - 1) / p.beta; // beta s <= 56 < 64: the slices fit one 64-bit word
     return p;
 }
 
-// Scale exponents: ex[r] = the least e with max_c |X(r, c)| < 2^e (0 for a zero line).
-// by_row: r indexes rows (max over columns); else r indexes columns (max over rows).
-__global__ void k_line_exponent(int n, const double *__restrict__ X, int ldx, bool by_row,
-                                int *ex) {
-    if (by_row) {
-        const int r = blockIdx.x * blockDim.x + threadIdx.x;
-        if (r >= n) return;
-        double m = 0.0;
-        for (int c = 0; c < n; ++c) m = fmax(m, fabs(X[(size_t)c * ldx + r]));
-        ex[r] = m > 0.0 ? ilogb(m) + 1 : 0;
-    } else {
-        // one warp per column
-        const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-        const int lane = threadIdx.x & 31;
-        if (c >= n) return;
-        double m = 0.0;
-        for (int r = lane; r < n; r += 32) m = fmax(m, fabs(X[(size_t)c * ldx + r]));
-        for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0) ex[c] = m > 0.0 ? ilogb(m) + 1 : 0;
-    }
+// x 2^e exactly (up to the rounding of a subnormal result) by two power-of-two factors.
+__device__ __forceinline__ double scale2(double x, int e) {
+    e = max(-2044, min(2046, e));
+    const int e1 = e / 2, e2 = e - e1;
+    return x * pow2i(e1) * pow2i(e2);
 }
 
-// Slices of X (n x n, column-major): x 2^-e = sum_p a_p 2^(-beta (p+1)) + rest, a_p integers,
-// written as bf16 planes S[p] (column-major, leading dimension n).  e per row or column.
+// Largest |X| per row (by_row) or per column, as the bit pattern of the binary64 value
+// (for non-negative doubles the integer order is the numeric order).  Blocks of 32 rows x 8
+// column lanes, each block over 256 columns; mx must start at zero.
+__global__ void k_line_max(int n, const double *__restrict__ X, int ldx, bool by_row,
+                           unsigned long long *mx) {
+    const int r = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int cl = threadIdx.x >> 5;
+    const int c0 = blockIdx.y * 256;
+    unsigned long long m = 0;
+    for (int t = 0; t < 32; ++t) {
+        const int c = c0 + t * 8 + cl;
+        unsigned long long v = 0;
+        if (r < n && c < n) v = (unsigned long long)__double_as_longlong(X[(size_t)c * ldx + r]) & 0x7fffffffffffffffull;
+        if (by_row) {
+            m = v > m ? v : m;
+        } else {
+            for (int o = 16; o; o >>= 1) {
+                const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
+                v = u > v ? u : v;
+            }
+            if ((threadIdx.x & 31) == 0 && c < n && v) atomicMax(mx + c, v);
+        }
+    }
+    if (by_row && r < n && m) atomicMax(mx + r, m);
+}
+
+// ex[r] = the least e with max |X(line r)| < 2^e (0 for a zero line; a non-finite maximum
+// gives 0 too, and its slices carry the NaN).
+__global__ void k_line_exponent(int n, const unsigned long long *__restrict__ mx, int *ex) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const unsigned long long b = mx[r];
+    const int eb = (int)(b >> 52);
+    int e = 0;
+    if (b == 0 || eb == 0x7ff) e = 0;
+    else if (eb == 0) e = (63 - __clzll((long long)b)) - 1073; // subnormal maximum
+    else e = eb - 1022;
+    ex[r] = e;
+}
+
+// Slices of X (n x n, column-major) by integer arithmetic: |x| 2^-e < 1 is read as the
+// 64-bit fixed-point fraction F (its bits below 2^-64 truncated), slice p is bits
+// [64 - beta (p+1), 64 - beta p) of F with the sign of x, an integer of magnitude < 2^beta,
+// written as bf16 to plane S[p] (column-major, leading dimension n).  Hence
+// x 2^-e = sum_p a_p 2^(-beta (p+1)) + r with |r| < 2^(-beta s).
 __global__ void k_slice(int n, const double *__restrict__ X, int ldx, const int *__restrict__ ex,
-                        bool by_row, int beta, int s, __nv_bfloat16 *S) {
+                        bool by_row, int beta, int s, unsigned short *S) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)n * n) return;
     const int c = (int)(idx / n), r = (int)(idx % n);
-    double x = ldexp(X[(size_t)c * ldx + r], -(by_row ? ex[r] : ex[c]));
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(X[(size_t)c * ldx + r]);
+    const unsigned sgn = (unsigned)(bits >> 63) << 15;
+    const int eb = (int)((bits >> 52) & 0x7ff);
     const size_t plane = (size_t)n * n;
+    if (eb == 0x7ff) { // NaN or infinity: propagate a NaN through the products
+        for (int p = 0; p < s; ++p) S[p * plane + idx] = (unsigned short)0x7fc0;
+        return;
+    }
+    const unsigned long long m = eb ? ((bits & 0xfffffffffffffull) | (1ull << 52)) : (bits & 0xfffffffffffffull);
+    const int E = eb ? eb - 1075 : -1074;
+    const int sh = E + 64 - (by_row ? ex[r] : ex[c]);
+    const unsigned long long F = sh >= 0 ? (m << sh) : (-sh >= 64 ? 0ull : (m >> -sh));
+    const unsigned mask = (1u << beta) - 1u;
     for (int p = 0; p < s; ++p) {
-        const double y = ldexp(x, beta);
-        const double a = rint(y);
-        S[p * plane + idx] = __double2bfloat16(a);
-        x = y - a;
+        const unsigned v = (unsigned)(F >> (64 - beta * (p + 1))) & mask;
+        unsigned short h = 0;
+        if (v) {
+            const int e2 = 31 - __clz((int)v);
+            h = (unsigned short)(sgn | ((unsigned)(e2 + 127) << 7) | ((v << (7 - e2)) & 0x7fu));
+        }
+        S[p * plane + idx] = h;
     }
 }
 
-// acc(i, k) += sum_{q < nq} 2^(-beta (p + q + 2)) Cp(i, q n + k)  (Cp: n x nq n, FP32, ld n).
+// acc(i, k) += sum_{q < nq} 2^(-beta (p + q + 2)) Cp(i, q n + k)  (Cp: n x nq n, FP32, ld n;
+// each Cp entry an exact integer, the terms added from the smallest weight up).
 __global__ void k_ozaki_accumulate(int n, int nq, int p, int beta, const float *__restrict__ Cp,
                                    double *acc) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)n * n) return;
     const size_t plane = (size_t)n * n;
     double t = 0.0;
-    for (int q = nq - 1; q >= 0; --q) t += ldexp((double)Cp[q * plane + idx], -beta * (p + q + 2));
+    for (int q = nq - 1; q >= 0; --q)
+        t = fma((double)__ldg(Cp + q * plane + idx), pow2i(-beta * (p + q + 2)), t);
     acc[idx] += t;
 }
 
@@ -213,7 +221,7 @@ __global__ void k_ozaki_finish_F(int n, const int *__restrict__ ea, const int *_
     const int k = (int)(idx / n), i = (int)(idx % n);
     if (i == k) { acc[idx] = 0.0; return; }
     const double D = w[k] - w[i];
-    acc[idx] = ldexp(acc[idx], ea[i] + eb[k]) * (D / (D * D + delta * delta));
+    acc[idx] = scale2(acc[idx], ea[i] + eb[k]) * (D / fma(D, D, delta * delta));
 }
 
 // Y = 2^(ea_j + eb_k) acc in place (Y = Z B stage).
@@ -222,7 +230,7 @@ __global__ void k_ozaki_finish_scale(int n, const int *__restrict__ ea, const in
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)n * n) return;
     const int k = (int)(idx / n), j = (int)(idx % n);
-    acc[idx] = ldexp(acc[idx], ea[j] + eb[k]);
+    acc[idx] = scale2(acc[idx], ea[j] + eb[k]);
 }
 
 // One cuBLAS handle per device, created on first use; the mutex serialises its users.
@@ -237,21 +245,21 @@ cublasHandle_t blas_for_current_device() {
 }
 
 // acc = op(A) * B summed exactly slice by slice; transA: op(A) = A^T with A's columns
-// scaled (ea), else op(A) = A with A's rows scaled (ea); B's columns scaled (eb).
-// SA, SB: s planes of n x n bf16 each; Cbuf: n x s n floats.
+// scaled, else op(A) = A with A's rows scaled; B's columns scaled.  SA, SB: s planes of
+// n x n bf16 each; Cbuf: n x s n floats.
 int ozaki_product(cublasHandle_t h, int n, const OzakiPlan &pl, bool transA,
-                  const __nv_bfloat16 *SA, const __nv_bfloat16 *SB, float *Cbuf, double *acc,
+                  const unsigned short *SA, const unsigned short *SB, float *Cbuf, double *acc,
                   cudaStream_t st) {
     const size_t plane = (size_t)n * n;
     const unsigned nblk = (unsigned)((plane + 255) / 256);
     const float one = 1.f, zero = 0.f;
-    cudaMemsetAsync(acc, 0, sizeof(double) * plane, st);
+    if (cudaMemsetAsync(acc, 0, sizeof(double) * plane, st) != cudaSuccess) return MR3_ECUDA;
     for (int c0 = 0; c0 < n; c0 += pl.chunk) {
         const int kc = std::min(pl.chunk, n - c0);
         for (int p = pl.s - 1; p >= 0; --p) {
             const int nq = pl.s - p; // slices q with p + q <= s - 1
-            const __nv_bfloat16 *A = SA + p * plane + (transA ? (size_t)c0 : (size_t)c0 * n);
-            const __nv_bfloat16 *B = SB + c0;
+            const unsigned short *A = SA + p * plane + (transA ? (size_t)c0 : (size_t)c0 * n);
+            const unsigned short *B = SB + c0;
             const cublasStatus_t rc = cublasGemmEx(
                 h, transA ? CUBLAS_OP_T : CUBLAS_OP_N, CUBLAS_OP_N, n, nq * n, kc, &one, A,
                 CUDA_R_16BF, n, B, CUDA_R_16BF, n, &zero, Cbuf, CUDA_R_32F, n,
@@ -263,58 +271,127 @@ int ozaki_product(cublasHandle_t h, int n, const OzakiPlan &pl, bool transA,
     return 0;
 }
 
-// Vector part of the backward for n >= kOzakiMinN: dd, de += diag terms of Z (F o Z^T G) Z^T.
-int backward_vectors_ozaki(int n, const double *w, const double *Z, int ldz, const double *gZ,
-                           int ldgz, double delta, double *dd, double *de, cudaStream_t st) {
+// Row reductions onto d and e, in two passes with a fixed summation order: blocks of 32
+// rows x 8 column lanes write one partial sum per row and column chunk, then
+// k_rows_finish adds the chunks.
+//   kind 0 (eigenvalue part): sd_j = sum_i g_i Z_ji^2,  se_j = 2 sum_i g_i Z_ji Z_j+1,i
+//   kind 1 (vector part):     sd_j = sum_b Y_jb Z_jb,   se_j = sum_b Y_jb Z_j+1,b + Y_j+1,b Z_jb
+constexpr int kRowChunks = 32;
+
+template <int KIND>
+__global__ void __launch_bounds__(256) k_row_dots(int n, int ncols, const double *__restrict__ Y,
+                                                  int ldy, const double *__restrict__ Z, int ldz,
+                                                  const double *__restrict__ g, double *pd,
+                                                  double *pe) {
+    __shared__ double sd_s[8][33], se_s[8][33];
+    const int tr = threadIdx.x & 31, cl = threadIdx.x >> 5;
+    const int j = blockIdx.x * 32 + tr;
+    const int per = (ncols + kRowChunks - 1) / kRowChunks;
+    const int b0 = blockIdx.y * per, b1 = min(ncols, b0 + per);
+    double sd = 0.0, se = 0.0;
+    if (j < n) {
+        for (int b = b0 + cl; b < b1; b += 8) {
+            const double *zc = Z + (size_t)b * ldz;
+            const double z = zc[j];
+            const double z1 = (j + 1 < n) ? zc[j + 1] : 0.0;
+            if (KIND == 0) {
+                const double gz = __ldg(g + b) * z;
+                sd = fma(gz, z, sd);
+                se = fma(gz, z1, se);
+            } else {
+                const double *yc = Y + (size_t)b * ldy;
+                const double y = yc[j];
+                const double y1 = (j + 1 < n) ? yc[j + 1] : 0.0;
+                sd = fma(y, z, sd);
+                se = fma(y, z1, fma(y1, z, se));
+            }
+        }
+    }
+    sd_s[cl][tr] = sd;
+    se_s[cl][tr] = se;
+    __syncthreads();
+    if (cl == 0 && j < n) {
+        double a = 0.0, c = 0.0;
+        for (int q = 0; q < 8; ++q) { a += sd_s[q][tr]; c += se_s[q][tr]; }
+        pd[(size_t)blockIdx.y * n + j] = a;
+        pe[(size_t)blockIdx.y * n + j] = c;
+    }
+}
+
+// dd_j (=|+=) sum of the chunks' partial sums; de_j likewise with factor fe.
+__global__ void k_rows_finish(int n, const double *__restrict__ pd, const double *__restrict__ pe,
+                              double fe, bool add, double *dd, double *de) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double a = 0.0, c = 0.0;
+    for (int q = 0; q < kRowChunks; ++q) { a += pd[(size_t)q * n + j]; c += pe[(size_t)q * n + j]; }
+    if (add) {
+        dd[j] += a;
+        if (j < n - 1) de[j] += fe * c;
+    } else {
+        dd[j] = a;
+        if (j < n - 1) de[j] = fe * c;
+    }
+}
+
+// Y = Z (F o (Z^T G)) for n >= kOzakiMinN through the slice products (Y: n x n, ld n).
+int vector_part_ozaki(int n, const double *w, const double *Z, int ldz, const double *gZ,
+                      int ldgz, double delta, double *Y, cudaStream_t st) {
     const OzakiPlan pl = ozaki_plan(n);
     const size_t plane = (size_t)n * n;
-    __nv_bfloat16 *SA = nullptr, *SB = nullptr;
+    unsigned short *SA = nullptr, *SB = nullptr;
     float *Cbuf = nullptr;
-    double *acc = nullptr, *Y = nullptr;
+    double *acc = nullptr;
     int *ex = nullptr;
-    auto fail = [&](int code) {
+    unsigned long long *mx = nullptr;
+    auto done = [&](int code) {
         if (SA) cudaFreeAsync(SA, st);
         if (SB) cudaFreeAsync(SB, st);
         if (Cbuf) cudaFreeAsync(Cbuf, st);
         if (acc) cudaFreeAsync(acc, st);
-        if (Y) cudaFreeAsync(Y, st);
         if (ex) cudaFreeAsync(ex, st);
+        if (mx) cudaFreeAsync(mx, st);
         return code;
     };
-    if (cudaMallocAsync((void **)&SA, sizeof(__nv_bfloat16) * plane * pl.s, st) != cudaSuccess ||
-        cudaMallocAsync((void **)&SB, sizeof(__nv_bfloat16) * plane * pl.s, st) != cudaSuccess ||
+    if (cudaMallocAsync((void **)&SA, sizeof(unsigned short) * plane * pl.s, st) != cudaSuccess ||
+        cudaMallocAsync((void **)&SB, sizeof(unsigned short) * plane * pl.s, st) != cudaSuccess ||
         cudaMallocAsync((void **)&Cbuf, sizeof(float) * plane * pl.s, st) != cudaSuccess ||
         cudaMallocAsync((void **)&acc, sizeof(double) * plane, st) != cudaSuccess ||
-        cudaMallocAsync((void **)&Y, sizeof(double) * plane, st) != cudaSuccess ||
-        cudaMallocAsync((void **)&ex, sizeof(int) * 4 * n, st) != cudaSuccess) {
+        cudaMallocAsync((void **)&ex, sizeof(int) * 4 * n, st) != cudaSuccess ||
+        cudaMallocAsync((void **)&mx, sizeof(unsigned long long) * 4 * n, st) != cudaSuccess) {
         cudaGetLastError();
-        return fail(MR3_EOOM);
+        return done(MR3_EOOM);
     }
     int *ea = ex, *eb = ex + n, *ea2 = ex + 2 * n, *eb2 = ex + 3 * n;
+    unsigned long long *ma = mx, *mb = mx + n, *ma2 = mx + 2 * n, *mb2 = mx + 3 * n;
     const unsigned nblk = (unsigned)((plane + 255) / 256);
-    const unsigned wblk = (unsigned)((32ll * n + 255) / 256);
     const unsigned rblk = (unsigned)((n + 127) / 128);
+    const dim3 mgrid((n + 31) / 32, (n + 255) / 256);
+    if (cudaMemsetAsync(mx, 0, sizeof(unsigned long long) * 4 * n, st) != cudaSuccess) return done(MR3_ECUDA);
     std::lock_guard<std::mutex> lock(g_blas_mutex);
     cublasHandle_t h = blas_for_current_device();
-    if (!h || cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS) return fail(MR3_ECUDA);
+    if (!h || cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS) return done(MR3_ECUDA);
     // C = Z^T G: columns of Z and of G scaled
-    k_line_exponent<<<wblk, 256, 0, st>>>(n, Z, ldz, false, ea);
-    k_line_exponent<<<wblk, 256, 0, st>>>(n, gZ, ldgz, false, eb);
+    k_line_max<<<mgrid, 256, 0, st>>>(n, Z, ldz, false, ma);
+    k_line_max<<<mgrid, 256, 0, st>>>(n, gZ, ldgz, false, mb);
+    k_line_exponent<<<rblk, 128, 0, st>>>(n, ma, ea);
+    k_line_exponent<<<rblk, 128, 0, st>>>(n, mb, eb);
     k_slice<<<nblk, 256, 0, st>>>(n, Z, ldz, ea, false, pl.beta, pl.s, SA);
     k_slice<<<nblk, 256, 0, st>>>(n, gZ, ldgz, eb, false, pl.beta, pl.s, SB);
     int rc = ozaki_product(h, n, pl, true, SA, SB, Cbuf, acc, st);
-    if (rc) return fail(rc);
+    if (rc) return done(rc);
     k_ozaki_finish_F<<<nblk, 256, 0, st>>>(n, ea, eb, w, delta, acc);
     // Y = Z B: rows of Z and columns of B scaled
-    k_line_exponent<<<rblk, 128, 0, st>>>(n, Z, ldz, true, ea2);
-    k_line_exponent<<<wblk, 256, 0, st>>>(n, acc, n, false, eb2);
+    k_line_max<<<mgrid, 256, 0, st>>>(n, Z, ldz, true, ma2);
+    k_line_max<<<mgrid, 256, 0, st>>>(n, acc, n, false, mb2);
+    k_line_exponent<<<rblk, 128, 0, st>>>(n, ma2, ea2);
+    k_line_exponent<<<rblk, 128, 0, st>>>(n, mb2, eb2);
     k_slice<<<nblk, 256, 0, st>>>(n, Z, ldz, ea2, true, pl.beta, pl.s, SA);
     k_slice<<<nblk, 256, 0, st>>>(n, acc, n, eb2, false, pl.beta, pl.s, SB);
     rc = ozaki_product(h, n, pl, false, SA, SB, Cbuf, Y, st);
-    if (rc) return fail(rc);
+    if (rc) return done(rc);
     k_ozaki_finish_scale<<<nblk, 256, 0, st>>>(n, ea2, eb2, Y);
-    k_bwd_vec_reduce<<<rblk, 128, 0, st>>>(n, Y, Z, ldz, dd, de);
-    return fail(0);
+    return done(0);
 }
 
 } // namespace
@@ -336,39 +413,55 @@ extern "C" int mr3_backward(int n, int k, const double *w, const double *Z, int 
     if (n > 1 && !de) return -10;
     if (n == 0) return 0;
     cudaStream_t s = (cudaStream_t)stream;
-    k_bwd_eigvals<<<(n + 127) / 128, 128, 0, s>>>(n, k, Z, ldz, gw, dd, de);
-    if (gZ && n >= kOzakiMinN) {
-        double w0, wn;
-        cudaMemcpyAsync(&w0, w, sizeof(double), cudaMemcpyDeviceToHost, s);
-        cudaMemcpyAsync(&wn, w + n - 1, sizeof(double), cudaMemcpyDeviceToHost, s);
-        cudaStreamSynchronize(s);
-        const double tnorm = std::max(std::fabs(w0), std::fabs(wn));
-        const double delta = n * kEps * (tnorm > 0 ? tnorm : 1.0);
-        const int rc = backward_vectors_ozaki(n, w, Z, ldz, gZ, ldgz, delta, dd, de, s);
-        if (rc) return rc;
-    } else if (gZ && n > 1) {
-        double *C = nullptr, *Y = nullptr;
-        if (cudaMallocAsync((void **)&C, sizeof(double) * (size_t)n * n, s) != cudaSuccess ||
-            cudaMallocAsync((void **)&Y, sizeof(double) * (size_t)n * n, s) != cudaSuccess) {
-            cudaGetLastError();
-            if (C) cudaFreeAsync(C, s);
-            return MR3_EOOM;
-        }
+    double *part = nullptr, *C = nullptr, *Y = nullptr;
+    const bool vec = gZ && n > 1;
+    auto done = [&](int code) {
+        if (part) cudaFreeAsync(part, s);
+        if (C) cudaFreeAsync(C, s);
+        if (Y) cudaFreeAsync(Y, s);
+        if (code == 0 && cudaStreamSynchronize(s) != cudaSuccess) { cudaGetLastError(); return (int)MR3_ECUDA; }
+        return code;
+    };
+    if (cudaMallocAsync((void **)&part, sizeof(double) * 2 * kRowChunks * (size_t)n, s) != cudaSuccess ||
+        (vec && cudaMallocAsync((void **)&Y, sizeof(double) * (size_t)n * n, s) != cudaSuccess) ||
+        (vec && n < kOzakiMinN && cudaMallocAsync((void **)&C, sizeof(double) * (size_t)n * n, s) != cudaSuccess)) {
+        cudaGetLastError();
+        return done(MR3_EOOM);
+    }
+    double *pd = part, *pe = part + (size_t)kRowChunks * n;
+    const dim3 rgrid((n + 31) / 32, kRowChunks);
+    const unsigned fblk = (unsigned)((n + 127) / 128);
+    // eigenvalue part: dbar_j = sum_i g_i z_ji^2, ebar_j = 2 sum_i g_i z_ji z_j+1,i
+    if (gw && k > 0) {
+        k_row_dots<0><<<rgrid, 256, 0, s>>>(n, k, nullptr, 1, Z, ldz, gw, pd, pe);
+        k_rows_finish<<<fblk, 128, 0, s>>>(n, pd, pe, 2.0, false, dd, de);
+    } else {
+        if (cudaMemsetAsync(dd, 0, sizeof(double) * n, s) != cudaSuccess ||
+            (n > 1 && cudaMemsetAsync(de, 0, sizeof(double) * (n - 1), s) != cudaSuccess))
+            return done(MR3_ECUDA);
+    }
+    if (vec) {
         // ||T|| from the eigenvalues (ascending): max(|lambda_1|, |lambda_n|)
         double w0, wn;
-        cudaMemcpyAsync(&w0, w, sizeof(double), cudaMemcpyDeviceToHost, s);
-        cudaMemcpyAsync(&wn, w + n - 1, sizeof(double), cudaMemcpyDeviceToHost, s);
-        cudaStreamSynchronize(s);
+        if (cudaMemcpyAsync(&w0, w, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaMemcpyAsync(&wn, w + n - 1, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaGetLastError();
+            return done(MR3_ECUDA);
+        }
         const double tnorm = std::max(std::fabs(w0), std::fabs(wn));
         const double delta = n * kEps * (tnorm > 0 ? tnorm : 1.0);
-        dim3 g((n + 63) / 64, (n + 63) / 64);
-        k_gemm_f64<true><<<g, 256, 0, s>>>(n, n, n, Z, ldz, gZ, ldgz, C, n);
-        k_apply_F<<<(unsigned)(((long long)n * n + 255) / 256), 256, 0, s>>>(n, w, delta, C);
-        k_gemm_f64<false><<<g, 256, 0, s>>>(n, n, n, Z, ldz, C, n, Y, n);
-        k_bwd_vec_reduce<<<(n + 127) / 128, 128, 0, s>>>(n, Y, Z, ldz, dd, de);
-        cudaFreeAsync(C, s);
-        cudaFreeAsync(Y, s);
+        if (n >= kOzakiMinN) {
+            const int rc = vector_part_ozaki(n, w, Z, ldz, gZ, ldgz, delta, Y, s);
+            if (rc) return done(rc);
+        } else {
+            dim3 g((n + 63) / 64, (n + 63) / 64);
+            k_gemm_f64<true><<<g, 256, 0, s>>>(n, n, n, Z, ldz, gZ, ldgz, C, n);
+            k_apply_F<<<(unsigned)(((long long)n * n + 255) / 256), 256, 0, s>>>(n, w, delta, C);
+            k_gemm_f64<false><<<g, 256, 0, s>>>(n, n, n, Z, ldz, C, n, Y, n);
+        }
+        k_row_dots<1><<<rgrid, 256, 0, s>>>(n, n, Y, n, Z, ldz, nullptr, pd, pe);
+        k_rows_finish<<<fblk, 128, 0, s>>>(n, pd, pe, 1.0, true, dd, de);
     }
-    if (cudaStreamSynchronize(s) != cudaSuccess) { cudaGetLastError(); return MR3_ECUDA; }
-    return 0;
+    return done(0);
 }
