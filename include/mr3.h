@@ -47,7 +47,12 @@ typedef enum {
 } mr3_range;
 
 /* Internal arithmetic of the representation tree (Ch. 5: FP64 in and out, the
- * tree either in FP64 or in double-double). */
+ * tree either in FP64 or in double-double).  MR3_DD: representations, shifts
+ * (dstqds), twisted factorizations and the Rayleigh-quotient iteration in
+ * double-double (unit roundoff ~2^-104); eigenvalue approximation by bisection in
+ * binary64 on the representations' leading words; gaptol 1e-10 by default; the RQI
+ * stops at a local residual of gap * eps * sqrt(n).  Expected orthogonality
+ * ~eps sqrt(n) instead of the FP64 tree's O(n eps / gaptol) worst case. */
 typedef enum { MR3_FP64 = 0, MR3_DD = 1 } mr3_precision;
 
 /* Options; a zero-initialised struct (or NULL) selects the defaults in brackets. */
@@ -196,8 +201,9 @@ int mr3_backward(int n, int k, const double *w, const double *Z, int ldz, const 
  * counterpart; this entry point exists for callers that cannot let a library allocate
  * (their device memory is claimed in full up front, or no allocator may be entered).
  *
- *  Arguments, outputs, defaults and return codes as for mr3_stemr; opts->profile is
- *  ignored (kernel_ms and kernel_launches stay zero).  Every step runs on `stream`.
+ *  Arguments, outputs, defaults and return codes as for mr3_stemr, except that
+ *  opts->prec must be MR3_FP64 (else -13) and opts->profile is ignored (kernel_ms and
+ *  kernel_launches stay zero).  Every step runs on `stream`.
  *  Extra return code: MR3_ENOSCRATCH when n > MR3_STATIC_MAX_N (checked before any
  *  device work), or when the representation tree of this matrix needs more room than
  *  the array has (then w and Z are undefined, *m = 0, and the stream is idle on return).

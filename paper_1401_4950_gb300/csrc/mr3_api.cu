@@ -208,8 +208,12 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
         if (info) *info = out;
         return 0;
     }
-    // ---- root representations and level-0 intervals
-    double *pool0 = ws.get<double>((size_t)kRepStride * nrows + (size_t)kRepPad * nblk);
+    // ---- root representations and level-0 intervals.  With the double-double tree a
+    // pool holds a second plane of low-order words right behind the leading ones.
+    const bool dd = (o.prec == MR3_DD);
+    const size_t pool0_len = (size_t)kRepStride * nrows + (size_t)kRepPad * nblk;
+    double *pool0 = ws.get<double>(dd ? 2 * pool0_len : pool0_len);
+    double *pool0_lo = dd && pool0 ? pool0 + pool0_len : nullptr;
     int *grid = ws.get<int>(ncols + 64ll * nblk + 1);
     float *f32 = ws.get<float>(2 * nrows);
     Node *nodes0 = ws.get<Node>(nblk);
@@ -228,6 +232,7 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
     CK(cudaMemsetAsync(cnode, 0xff, sizeof(int) * ncols, s));
     tk = prof.begin();
     launch_root(nblk, blks, d, e, pool0, f32, o.seed, s);
+    if (dd) launch_root_dd(nblk, blks, d, e, pool0, pool0_lo, o.seed, s);
     launch_init_columns(nblk, blks, nodes0, cnode, jloc, lo, hi, (int)ncols, s);
     prof.end(tk, 1, 2);
     const double rtol = 1e-2 * o.gaptol;
@@ -273,18 +278,20 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
     std::vector<Pending> pending;   // pools/nodes still read by an RQI launch
     std::vector<cudaEvent_t> rqi_done(2, nullptr);
     Node *cur_nodes = nodes0;
-    double *cur_pool = pool0;
+    double *cur_pool = pool0, *cur_lo = pool0_lo;
     int ncur = nblk;
     double *scratch = nullptr;
     long long scratch_slots = 0;
     const long long scratch_cap_bytes = 2ll << 30; // RQI scratch budget per launch
     int status = 0;
     auto run_singles = [&](int level, const LevelCounters &hc) -> int {
-        long long slots = rqi_slots(hc.nsingle, nmax, scratch_cap_bytes);
+        long long slots = dd ? rqi_dd_threads(hc.nsingle, nmax, 2 * scratch_cap_bytes)
+                             : rqi_slots(hc.nsingle, nmax, scratch_cap_bytes);
+        const size_t per_slot = dd ? (size_t)4 * nmax : (size_t)rqi_scratch_per_index() * nmax;
         if (slots > scratch_slots) {
             if (scratch) cudaFreeAsync(scratch, side); // after the side stream's last use
             void *p = nullptr;
-            if (cudaMallocAsync(&p, (size_t)slots * rqi_scratch_per_index() * nmax * sizeof(double), s) != cudaSuccess) {
+            if (cudaMallocAsync(&p, (size_t)slots * per_slot * sizeof(double), s) != cudaSuccess) {
                 cudaGetLastError();
                 scratch = nullptr;
                 return MR3_EOOM;
@@ -296,9 +303,14 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
         cudaEventRecord(ready, s);
         cudaStreamWaitEvent(side, ready, 0);
         const int tq = prof.begin(side);
-        launch_rqi(hc.nsingle, singles2[level & 1], cur_nodes, blks, dmats, cur_pool, jloc, lo, hi,
-                   gapl, gapr, d, e, w, Z, scratch, (int)slots, nmax, o.max_rqi, o.fault_mask,
-                   work, dinfo, side);
+        if (dd)
+            launch_rqi_dd(hc.nsingle, singles2[level & 1], cur_nodes, blks, dmats, cur_pool, cur_lo,
+                          jloc, lo, hi, gapl, gapr, d, e, w, Z, scratch, slots, o.max_rqi,
+                          o.fault_mask, dinfo, side);
+        else
+            launch_rqi(hc.nsingle, singles2[level & 1], cur_nodes, blks, dmats, cur_pool, jloc, lo,
+                       hi, gapl, gapr, d, e, w, Z, scratch, (int)slots, nmax, o.max_rqi,
+                       o.fault_mask, work, dinfo, side);
         prof.end(tq, 4, 1, side);
         cudaEvent_t done = guard.make();
         cudaEventRecord(done, side);
@@ -324,7 +336,8 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
         }
         if (hc.ncluster == 0) break;
         const bool at_cap = (level + 1 >= o.max_depth);
-        double *next_pool = ws.get<double>((size_t)hc.pool_need);
+        double *next_pool = ws.get<double>(dd ? 2 * (size_t)hc.pool_need : (size_t)hc.pool_need);
+        double *next_lo = dd && next_pool ? next_pool + hc.pool_need : nullptr;
         Node *next_nodes = ws.get<Node>(hc.ncluster);
         double *tau = ws.get<double>(hc.ncluster);
         int *next_active = ws.get<int>(hc.nactive);
@@ -334,7 +347,10 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
         launch_shift(hc.ncluster, clusters, crep, cur_nodes, blks, cur_pool, next_pool,
                      next_nodes, tau, cnode, next_active, jloc, lo, hi, o.max_tries, o.fault_mask,
                      dinfo, s);
-        prof.end(tk, 5, 2);
+        if (dd)
+            launch_shift_dd(hc.ncluster, clusters, crep, cur_nodes, blks, cur_pool, cur_lo, next_pool,
+                            next_lo, next_nodes, tau, dinfo, s);
+        prof.end(tk, 5, dd ? 3 : 2);
         tk = prof.begin();
         launch_bisect(hc.nactive, next_active, lanes_for(hc.nactive, o), (int)ncols, cnode,
                       next_nodes, blks, next_pool, jloc, lo, hi, rtol, tau, dinfo, s);
@@ -349,6 +365,7 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
         pending.clear();
         pending.push_back({cur_pool, cur_nodes, level_rqi});
         cur_pool = next_pool;
+        cur_lo = next_lo;
         cur_nodes = next_nodes;
         ncur = hc.ncluster;
         if (at_cap) {

@@ -201,15 +201,23 @@ __global__ void k_slice(int n, const double *__restrict__ X, int ldx, const int 
 }
 
 // acc(i, k) += sum_{q < nq} 2^(-beta (p + q + 2)) Cp(i, q n + k)  (Cp: n x nq n, FP32, ld n;
-// each Cp entry an exact integer, the terms added from the smallest weight up).
+// each Cp entry an exact integer of magnitude < 2^24).  Up to G consecutive terms are first
+// combined exactly in a 64-bit integer (Horner in powers of 2^beta: below 2^(25 + beta (G-1))
+// <= 2^62), so the binary64 pipe sees one conversion and one FMA per group; groups are added
+// from the smallest weight up.
 __global__ void k_ozaki_accumulate(int n, int nq, int p, int beta, const float *__restrict__ Cp,
                                    double *acc) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)n * n) return;
     const size_t plane = (size_t)n * n;
+    const int G = 1 + 37 / beta;
     double t = 0.0;
-    for (int q = nq - 1; q >= 0; --q)
-        t = fma((double)__ldg(Cp + q * plane + idx), pow2i(-beta * (p + q + 2)), t);
+    for (int q1 = nq; q1 > 0; q1 -= G) {
+        const int q0 = max(0, q1 - G);
+        long long S = 0;
+        for (int q = q0; q < q1; ++q) S = S * (1ll << beta) + (long long)__float2int_rn(__ldg(Cp + q * plane + idx));
+        t = fma((double)S, pow2i(-beta * (p + q1 + 1)), t);
+    }
     acc[idx] += t;
 }
 

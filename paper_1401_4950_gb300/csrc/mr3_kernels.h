@@ -81,4 +81,22 @@ void launch_rqi(int nsingle, const SingleItem *singles, const Node *nodes, const
 int rqi_scratch_per_index();
 int rqi_singles_per_slot();
 
+// ---- double-double representation tree (mr3_ddpath.cu, opts->prec = MR3_DD).  A pool
+// holding representations keeps the leading words in the binary64 layout and the low
+// words in a second plane at the same offsets (pool_lo).
+void launch_root_dd(int nblk, BlkDesc *blks, const double *d, const double *e, double *pool0,
+                    double *pool0_lo, unsigned long long seed, cudaStream_t s);
+void launch_shift_dd(int ncluster, const ClusterItem *clusters, const long long *cluster_rep,
+                     const Node *nodes, const BlkDesc *blks, const double *pool,
+                     const double *pool_lo, double *childpool, double *childpool_lo,
+                     Node *child_nodes, const double *child_tau, DevInfo *info, cudaStream_t s);
+// Threads for a singleton launch within a scratch budget (4 nmax doubles per thread).
+long long rqi_dd_threads(long long nsingle, int nmax, long long cap_bytes);
+void launch_rqi_dd(int nsingle, const SingleItem *singles, const Node *nodes, const BlkDesc *blks,
+                   const MatDesc *mats, const double *pool, const double *pool_lo, const int *jloc,
+                   const double *lo, const double *hi, const double *gapl, const double *gapr,
+                   const double *d, const double *e, double *w, double *Z, double *scratch,
+                   long long nthreads, int max_rqi, unsigned fault_mask, DevInfo *info,
+                   cudaStream_t s);
+
 } // namespace mr3

@@ -117,8 +117,7 @@ int lanes_auto(long long nactive, int tpe) {
 // The solve of one matrix (M filled in by the entry point) on the array behind `ar`.
 int solve_static(MatDesc &M, const double *d, const double *e, int range, double *w, double *Z,
                  const mr3_opts *opts, mr3_info &out, Arena &ar, cudaStream_t s) {
-    const bool dd = opts && opts->prec == MR3_DD;
-    const double gaptol = (opts && opts->gaptol > 0.0) ? opts->gaptol : (dd ? 1e-10 : 1e-3);
+    const double gaptol = (opts && opts->gaptol > 0.0) ? opts->gaptol : 1e-3;
     const unsigned long long seed = (opts && opts->seed) ? opts->seed : 0x5EEDull;
     const int max_rqi = (opts && opts->max_rqi > 0) ? opts->max_rqi : 10;
     const int max_tries = (opts && opts->max_shift_tries > 0) ? opts->max_shift_tries : 8;
@@ -312,6 +311,7 @@ extern "C" int mr3_stemr_static(int n, const double *d, const double *e, int ran
     if (n > 0 && !w) return -10;
     if (n > 0 && !Z) return -11;
     if (ldz < std::max(1, n)) return -12;
+    if (opts && opts->prec == MR3_DD) return -13; // the binary64 tree only
     *m = 0;
     mr3_info out;
     std::memset(&out, 0, sizeof(out));

@@ -54,6 +54,7 @@ def check_eigenpairs(d, e, w, Z, il=1, iu=None, w_ref=None, tn=None, resid_gate=
         if np.any(sep):
             Za = M.align_signs(Zr, Z)
             verr = np.abs(Za - Zr).max(axis=0)
-            bound = 1e3 * n * EPS * tn / g
+            bound = np.full(len(g), np.inf)
+            np.divide(1e3 * n * EPS * tn, g, out=bound, where=g > 0)
             assert np.all(verr[sep] <= bound[sep]), (verr[sep].max(), bound[sep].min())
     return stats
