@@ -391,6 +391,60 @@ def run_backward(args):
                       "backward_ms": 1e3 * tb}), flush=True)
 
 
+def _gpu_gates(d, e, w, Z, tnorm):
+    """Scaled residual max ||T z - lambda z|| / (n eps ||T||) and orthogonality
+    max |Z^T Z - I| / (n eps), computed with plain torch operations on the device."""
+    import torch
+    n = d.shape[0]
+    TZ = d[:, None] * Z
+    TZ[:-1] += e[:n - 1, None] * Z[1:]
+    TZ[1:] += e[:n - 1, None] * Z[:-1]
+    R = TZ - Z * w[None, :]
+    resid = torch.linalg.vector_norm(R, dim=0).max().item() / (n * EPS * tnorm)
+    G = Z.T @ Z
+    G.diagonal().sub_(1.0)
+    orth = G.abs().max().item() / (n * EPS)
+    return resid, orth
+
+
+def run_subset(args):
+    """Subset workload: eigenpairs 8001..12000 of the n = 20000 glued Wilkinson matrix (W21+
+    blocks glued by 1e-8), binary64 tree vs double-double tree.  Prints one JSON line."""
+    import torch
+    import paper_1401_4950_gb300 as mr3
+    dev = torch.device("cuda", 0)
+    n, il, iu = 20000, 8001, 12000
+    d, e = tm.make("glued_wilkinson", n)
+    dt, et = torch.tensor(d, device=dev), torch.tensor(e, device=dev)
+    w1, _, _ = mr3.stemr(dt, et, rng="I", il=1, iu=1)
+    wn, _, _ = mr3.stemr(dt, et, rng="I", il=n, iu=n)
+    tnorm = max(abs(w1.item()), abs(wn.item()))
+    out = {"metric": "eigenpairs/s (n=20000 glued Wilkinson, eigenpairs 8001..12000)",
+           "unit": "eigenpairs/s", "config": {"workload": "MRRR subset, n=20000 glued W21+ "
+                                              "(e=1e-8 at joins), il=8001, iu=12000"}}
+    for name, prec in (("fp64", mr3.FP64), ("dd", mr3.DD)):
+        opts = mr3.make_opts(prec=prec, profile=1)
+        for _ in range(2):
+            mr3.stemr(dt, et, rng="I", il=il, iu=iu, opts=opts)
+        torch.cuda.synchronize()
+        reps = max(1, args.steps)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(reps):
+            w, Z, info = mr3.stemr(dt, et, rng="I", il=il, iu=iu, opts=opts)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / reps
+        resid, orth = _gpu_gates(dt, et, w, Z, tnorm)
+        out[name] = {"value": (iu - il + 1) / (ms * 1e-3), "ms": ms, "resid": resid,
+                     "orth": orth, "dmax": info["dmax"], "nclusters": info["nclusters"],
+                     "largest_cluster": info["largest_cluster"],
+                     "rqi_iters": info["rqi_iters"], "bisect_fallbacks": info["bisect_fallbacks"],
+                     "status": info["status"],
+                     "kernel_ms": [round(x, 3) for x in info["kernel_ms"]]}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -406,6 +460,8 @@ def main():
     ap.add_argument("--backward", action="store_true",
                     help="time the backward pass against the forward instead")
     ap.add_argument("--n-bwd", type=int, default=4096)
+    ap.add_argument("--subset", action="store_true",
+                    help="time the n=20000 glued Wilkinson subset, binary64 vs double-double")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -417,6 +473,9 @@ def main():
         return
     if args.backward:
         run_backward(args)
+        return
+    if args.subset:
+        run_subset(args)
         return
     run_gpu(args, args.config, rank, world)
 

@@ -349,10 +349,12 @@ void launch_shift_dd(int ncluster, const ClusterItem *clusters, const long long 
                                                   child_nodes, child_tau, info);
 }
 
+// Threads of a singleton launch: one per singleton, rounded up to whole blocks of 128,
+// within the scratch budget (the launch then loops over the singletons).
 long long rqi_dd_threads(long long nsingle, int nmax, long long cap_bytes) {
     const long long per = 4ll * nmax * (long long)sizeof(double);
-    const long long cap = std::max<long long>(128, cap_bytes / per);
-    return std::min<long long>(nsingle, cap);
+    const long long cap = std::max<long long>(128, (cap_bytes / per) / 128 * 128);
+    return std::min<long long>((nsingle + 127) / 128 * 128, cap);
 }
 
 void launch_rqi_dd(int nsingle, const SingleItem *singles, const Node *nodes, const BlkDesc *blks,
@@ -362,12 +364,12 @@ void launch_rqi_dd(int nsingle, const SingleItem *singles, const Node *nodes, co
                    long long nthreads, int max_rqi, unsigned fault_mask, DevInfo *info,
                    cudaStream_t s) {
     if (nsingle <= 0 || nthreads <= 0) return;
-    const int bs = 128;
-    const long long T = std::min<long long>(nthreads, nsingle);
-    // scratch holds 4 nmax doubles for each of nthreads threads; the grid uses at most that
-    const unsigned nb = (unsigned)(T / bs > 0 ? T / bs : 1);
-    const int threads = (T < bs) ? (int)T : bs;
-    k_rqi_dd<<<nb, threads, 0, s>>>(nsingle, singles, nodes, blks, mats, pool, pool_lo, jloc, lo,
+    // scratch holds 4 nmax doubles for each of nthreads threads (a multiple of 128, or
+    // fewer than 128); the grid uses at most that many and loops over the singletons
+    const int bs = (int)std::min<long long>(128, nthreads);
+    const long long need = (nsingle + bs - 1) / bs;
+    const unsigned nb = (unsigned)std::min<long long>(need, nthreads / bs);
+    k_rqi_dd<<<nb, bs, 0, s>>>(nsingle, singles, nodes, blks, mats, pool, pool_lo, jloc, lo,
                                      hi, gapl, gapr, d, e, w, Z, scratch, max_rqi, fault_mask,
                                      info);
 }
