@@ -174,6 +174,25 @@ def run_reference(args, cfg, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ ranks
+
+def max_over_ranks(ms, dist=None, device=None):
+    """The slowest rank's time (the job ends when its last rank does); `ms` unchanged on
+    one rank."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, ms_per_step):
+    """Whole-job throughput: every rank solves its own copy of the step's matrices (weak
+    scaling), so the job processes world * units_per_rank units per step."""
+    return world * units_per_rank / (ms_per_step / 1e3)
+
+
 # ------------------------------------------------------------------ GPU leg
 
 def run_gpu(args, cfg, rank, world):
@@ -231,13 +250,9 @@ def run_gpu(args, cfg, rank, world):
     wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    tot_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([tot_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = max_over_ranks(sum(step_ms), dist, dev)
     ms_per_step = tot_ms / args.steps
-    value = world * units_per_step / (ms_per_step / 1e3)
+    value = job_value(units_per_step, world, ms_per_step)
 
     # ---- dominant kernel and its roofline (FP64 pipe)
     g = agg["kernel_ms"]

@@ -60,7 +60,7 @@ typedef struct {
     int prec;                  /* mr3_precision [MR3_FP64]                                   */
     double gaptol;             /* classification threshold on reldist (Sec. 3.2.3)
                                   [1e-3 for FP64, 1e-10 for DD (Ch. 5, Eq. gaptolinterval)] */
-    unsigned long long seed;   /* stream of the root's random perturbation (Alg. MRRR line 2)
+    unsigned long long seed;   /* stream of the root's random perturbation (Alg. MRRR)
                                   [0x5EED]                                                   */
     int max_rqi;               /* Rayleigh-quotient iterations per singleton before the
                                   bisection fallback (Alg. S-task) [10]                      */

@@ -40,14 +40,17 @@ Opts resolve(const mr3_opts *o) {
 }
 
 // Lanes per eigenvalue for the multisection: enough lanes in flight to keep the SMs busy
-// (about 12 warps per SM on 152 SMs), at most 32; opts->tpe overrides.
+// (about MR3_BISECT_WARPS_PER_SM warps per SM on 152 SMs), at most 32; opts->tpe overrides.
+#ifndef MR3_BISECT_WARPS_PER_SM
+#define MR3_BISECT_WARPS_PER_SM 48
+#endif
 int lanes_for(long long nactive, const Opts &o) {
     if (o.tpe > 0) {
         int L = 1;
         while (L * 2 <= o.tpe && L < 32) L *= 2;
         return L;
     }
-    const long long target = 152ll * 32 * 12;
+    const long long target = 152ll * 32 * MR3_BISECT_WARPS_PER_SM;
     int L = 1;
     while (L < 32 && (long long)(2 * L) * nactive <= target) L *= 2;
     return L;
@@ -234,7 +237,7 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
     launch_root(nblk, blks, d, e, pool0, f32, o.seed, s);
     if (dd) launch_root_dd(nblk, blks, d, e, pool0, pool0_lo, o.seed, s);
     launch_init_columns(nblk, blks, nodes0, cnode, jloc, lo, hi, (int)ncols, s);
-    prof.end(tk, 1, 2);
+    prof.end(tk, 1, dd ? 3 : 2);
     const double rtol = 1e-2 * o.gaptol;
     if (range != MR3_RANGE_ALL) launch_outer_gaps(nblk, blks, nodes0, pool0, rtol, dinfo, s);
     bool any_multi = false;
@@ -340,22 +343,24 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
         double *next_lo = dd && next_pool ? next_pool + hc.pool_need : nullptr;
         Node *next_nodes = ws.get<Node>(hc.ncluster);
         double *tau = ws.get<double>(hc.ncluster);
+        double2 *tri = ws.get<double2>(2 * (size_t)hc.ncluster);
         int *next_active = ws.get<int>(hc.nactive);
         CKW(ws);
         tk = prof.begin();
-        launch_refine_ends(hc.ncluster, clusters, cur_nodes, blks, cur_pool, jloc, lo, hi, dinfo, s);
+        launch_refine_ends(hc.ncluster, clusters, cur_nodes, blks, cur_pool, jloc, lo, hi, tri, dinfo, s);
         launch_shift(hc.ncluster, clusters, crep, cur_nodes, blks, cur_pool, next_pool,
                      next_nodes, tau, cnode, next_active, jloc, lo, hi, o.max_tries, o.fault_mask,
-                     dinfo, s);
+                     tri, dinfo, s);
         if (dd)
             launch_shift_dd(hc.ncluster, clusters, crep, cur_nodes, blks, cur_pool, cur_lo, next_pool,
                             next_lo, next_nodes, tau, dinfo, s);
-        prof.end(tk, 5, dd ? 3 : 2);
+        prof.end(tk, 5, dd ? 5 : 4); // refine_ends x2, shift trials, shift (+ double-double recompute)
         tk = prof.begin();
         launch_bisect(hc.nactive, next_active, lanes_for(hc.nactive, o), (int)ncols, cnode,
                       next_nodes, blks, next_pool, jloc, lo, hi, rtol, tau, dinfo, s);
         prof.end(tk, 6, 1);
         ws.release(next_active);
+        ws.release(tri);
         // return representations no longer read: older levels whose RQI has finished
         for (auto &pnd : pending) {
             if (pnd.done) cudaStreamWaitEvent(s, pnd.done, 0);

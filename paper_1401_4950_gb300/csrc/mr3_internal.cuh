@@ -124,7 +124,7 @@ __device__ __forceinline__ bool is_finite(double x) {
 
 // Counter-based SplitMix64 (Steele, Lea, Flood 2014): output for counter i of stream
 // seed, mapped to a uniform double in (-1, 1).  Draws the random relative perturbation
-// of the root representation (Alg. MRRR line 2).
+// of the root representation (Alg. MRRR).
 __device__ __forceinline__ double splitmix_pm1(unsigned long long seed, unsigned long long i) {
     unsigned long long z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;

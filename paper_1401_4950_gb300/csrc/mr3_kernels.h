@@ -28,7 +28,7 @@ void launch_index_multi(int nmat, MatDesc *mats, BlkDesc *blks, const double *d,
                         const double *e, cudaStream_t s);
 // Per matrix: columns of each block and m.
 void launch_assign_columns(int nmat, MatDesc *mats, BlkDesc *blks, int range, cudaStream_t s);
-// Root representation of every block (Alg. MRRR lines 1-2).
+// Root representation of every block (Alg. MRRR, root representation and its perturbation).
 void launch_root(int nblk, BlkDesc *blks, const double *d, const double *e, double *pool0,
                  float *f32scratch, unsigned long long seed, cudaStream_t s);
 // Level-0 nodes, per-column state and starting intervals.
@@ -53,15 +53,17 @@ void launch_classify(int nnode, const Node *nodes, const BlkDesc *blks, const do
                      const double *hi, double gaptol, double *gapl, double *gapr,
                      SingleItem *singles, ClusterItem *clusters, long long *cluster_rep,
                      int *cnode, LevelCounters *ctr, DevInfo *info, cudaStream_t s);
-// Refine the two extreme eigenvalues of every cluster (Alg. "Shifting the spectrum" line 1).
+// Refine the two extreme eigenvalues of every cluster (Alg. "Shifting the spectrum", first step).
+// carry: 2 ncluster double2 of scratch.
 void launch_refine_ends(int ncluster, const ClusterItem *clusters, const Node *nodes,
                         const BlkDesc *blks, const double *pool, const int *jloc, double *lo,
-                        double *hi, DevInfo *info, cudaStream_t s);
+                        double *hi, double2 *carry, DevInfo *info, cudaStream_t s);
+// tri: scratch of 2 ncluster double2 (existence and growth of the first two candidates).
 void launch_shift(int ncluster, const ClusterItem *clusters, const long long *cluster_rep,
                   const Node *nodes, const BlkDesc *blks, const double *pool, double *childpool,
                   Node *child_nodes, double *child_tau, int *cnode, int *active_list,
                   const int *jloc, double *lo, double *hi, int max_tries, unsigned fault_mask,
-                  DevInfo *info, cudaStream_t s);
+                  double2 *tri, DevInfo *info, cudaStream_t s);
 // Ascending eigenvalues: running-maximum fix for single-block matrices, flags for the rest.
 void launch_order_flags(int nmat, const MatDesc *mats, double *w, int *flags, cudaStream_t s);
 // Sort the m eigenpairs of matrix mi (temporaries: m values, n x m entries, m ints).

@@ -12,7 +12,12 @@ namespace mr3 {
 #define FULL_MASK 0xffffffffu
 
 // Offset of the shifts from the cluster's end eigenvalues, in units of eps |lambda|
-// (Alg. "Shifting the spectrum" line 2 suggests 100).
+// (Alg. "Shifting the spectrum" suggests 100).
+// Lanes given to the cluster-end refinement: up to this many warps per SM.
+#ifndef MR3_REFINE_WARPS_PER_SM
+#define MR3_REFINE_WARPS_PER_SM 8
+#endif
+
 #ifndef MR3_TAU_OFFSET
 #define MR3_TAU_OFFSET 100.0
 #endif
@@ -368,18 +373,20 @@ void launch_classify(int nnode, const Node *nodes, const BlkDesc *blks, const do
 
 // ------------------------------------------------------------------ cluster ends
 
-// Alg. "Shifting the spectrum" line 1: refine the extreme eigenvalues of every cluster
+// Alg. "Shifting the spectrum", first step: refine the extreme eigenvalues of every cluster
 // before the shift.  A group of E lanes owns one end (group 2c: lambda_p, group 2c+1:
 // lambda_q of cluster c) and multisects it until the interval is below 1e-3 of a lower
 // bound on the gap to the inner neighbour (so that a shift just outside the interval
 // leaves that end well separated in the child) or at full accuracy (4 eps |lambda|).  The
 // bound starts from the neighbour's interval and tightens with every sample whose count
-// shows the neighbour on its far side.  Counts are double-float while the interval is
-// wider than 1e-11 relative, binary64 below.
+// shows the neighbour on its far side.  Two launches: phase 0 counts in double-float and
+// stops at 1e-11 relative width (the limit of its counts), phase 1 continues in binary64
+// with fewer lanes per end (the binary64 pipe, not latency, bounds it when ends are many).
 __global__ void k_refine_ends(int ncluster, const ClusterItem *__restrict__ clusters,
                               const Node *__restrict__ nodes, const BlkDesc *__restrict__ blks,
                               const double *__restrict__ pool, const int *__restrict__ jloc,
-                              double *lo, double *hi, int E, DevInfo *info) {
+                              double *lo, double *hi, int E, int phase, double2 *carry,
+                              DevInfo *info) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const int g = tid / E, k = lane % E, gbase = lane - k;
@@ -401,20 +408,22 @@ __global__ void k_refine_ends(int ncluster, const ClusterItem *__restrict__ clus
         L = lo[col];
         H = hi[col];
         nb = side ? hi[col - 1] : lo[col + 1];
+        // phase 1 resumes with the neighbour bound phase 0 tightened
+        if (phase == 1) nb = carry[g].x;
     }
     unsigned long long steps = 0;
     for (int sweep = 0; sweep < 64; ++sweep) {
         const double w = H - L;
         const double gap_lb = side ? (L - nb) : (nb - H);
-        const double tol = fmax(4.0 * kEps * fmax(fabs(L), fabs(H)), 1e-3 * fmax(gap_lb, 0.0));
+        double tol = fmax(4.0 * kEps * fmax(fabs(L), fabs(H)), 1e-3 * fmax(gap_lb, 0.0));
+        if (phase == 0) tol = fmax(tol, 1e-11 * fmax(fabs(L), fabs(H)));
         bool done = !active || !(w > tol);
         const double x = L + (k + 1) * (w / (E + 1));
         if (__ballot_sync(0xffffffffu, !(x > L && x < H)) & gmask) done = true;
         if (__all_sync(0xffffffffu, done)) break;
         int cnt = 0;
         if (!done) {
-            cnt = (w > 1e-11 * fmax(fabs(L), fabs(H))) ? node_count(P, n, pd, x)
-                                                        : negcount_ldl(n, pd, pd + 2 * n, x);
+            cnt = (phase == 0) ? node_count(P, n, pd, x) : negcount_ldl(n, pd, pd + 2 * n, x);
             steps += n;
         }
         const unsigned bal = __ballot_sync(0xffffffffu, cnt < tgt);
@@ -437,6 +446,7 @@ __global__ void k_refine_ends(int ncluster, const ClusterItem *__restrict__ clus
     if (active && k == 0) {
         lo[col] = L;
         hi[col] = H;
+        if (phase == 0) carry[g] = make_double2(nb, 0.0);
     }
     for (int o = 16; o > 0; o >>= 1) steps += __shfl_xor_sync(0xffffffffu, steps, o);
     if (lane == 0 && steps) atomicAdd(&info->shift_steps, steps);
@@ -444,16 +454,19 @@ __global__ void k_refine_ends(int ncluster, const ClusterItem *__restrict__ clus
 
 void launch_refine_ends(int ncluster, const ClusterItem *clusters, const Node *nodes,
                         const BlkDesc *blks, const double *pool, const int *jloc, double *lo,
-                        double *hi, DevInfo *info, cudaStream_t s) {
+                        double *hi, double2 *carry, DevInfo *info, cudaStream_t s) {
     if (ncluster <= 0) return;
     // lanes per end: many ends -> fewer lanes (throughput), few ends -> more (latency)
     const long long ends = 2ll * ncluster;
-    int E = 4;
-    while (E < 32 && ends * (2 * E) <= 152ll * 32 * 8) E *= 2;
-    const long long threads = ends * E;
     const int bs = 64;
-    k_refine_ends<<<(unsigned)((threads + bs - 1) / bs), bs, 0, s>>>(ncluster, clusters, nodes, blks,
-                                                                     pool, jloc, lo, hi, E, info);
+    for (int phase = 0; phase < 2; ++phase) {
+        const long long cap = 152ll * 32 * (phase == 0 ? MR3_REFINE_WARPS_PER_SM : 2);
+        int E = phase == 0 ? 4 : 2;
+        while (E < 32 && ends * (2 * E) <= cap) E *= 2;
+        const long long threads = ends * E;
+        k_refine_ends<<<(unsigned)((threads + bs - 1) / bs), bs, 0, s>>>(
+            ncluster, clusters, nodes, blks, pool, jloc, lo, hi, E, phase, carry, info);
+    }
 }
 
 // ------------------------------------------------------------------ cluster shift
@@ -471,8 +484,8 @@ __device__ void trial_shift(int n, const double *__restrict__ d, const double *_
     for (int i = 0; i < n; ++i) {
         double c = fma(__ldg(d + i), cp, a);
         if (is_zero(c)) { ok = false; c = -cp * 0x1p-80; }
-        const double dp = c / cp;
-        g = fmax(g, fabs(dp));
+        // running max of |c_i / c_{i-1}|, dividing only when it may grow
+        if (fabs(c) > g * fabs(cp)) g = fmax(g, fabs(c / cp));
         if (!is_finite(c)) ok = false;
         int k = 0;
         if (i < n - 1) {
@@ -498,10 +511,45 @@ __device__ void trial_shift(int n, const double *__restrict__ d, const double *_
     growth = exists ? g : INFINITY;
 }
 
+// The first two candidates of every cluster, one lane each (16 clusters per warp):
+// tau_l = lo_p - 100 eps |lo_p| on even lanes, tau_r = hi_q + 100 eps |hi_q| on odd lanes.
+// Each stores its c_i and rescale exponents in the child's slots (tau_l: d, tau_r: dl;
+// exponents interleaved in dll) for the conversion, and its existence and growth in
+// tri[2 ci + side].
+__global__ void k_shift_trials(int ncluster, const ClusterItem *__restrict__ clusters,
+                               const long long *__restrict__ cluster_rep,
+                               const Node *__restrict__ nodes, const BlkDesc *__restrict__ blks,
+                               const double *__restrict__ pool, double *childpool,
+                               const double *__restrict__ lo, const double *__restrict__ hi,
+                               unsigned fault_mask, double2 *tri, DevInfo *info) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ci = t >> 1, side = t & 1;
+    unsigned long long steps = 0;
+    if (ci < ncluster) {
+        const ClusterItem C = clusters[ci];
+        const Node P = nodes[C.node];
+        const int n = blks[P.blk].n;
+        const double *pd = pool + P.rep;
+        double *cd = childpool + cluster_rep[ci];
+        const double Lp = lo[C.c0], Hq = hi[C.c1];
+        double tau = side ? Hq + MR3_TAU_OFFSET * kEps * fabs(Hq) : Lp - MR3_TAU_OFFSET * kEps * fabs(Lp);
+        if (side == 0 && (fault_mask & MR3_FAULT_NAN_SHIFT)) tau = NAN;
+        bool ex = false;
+        double g = INFINITY;
+        trial_shift(n, pd, pd + 2 * n, tau, true, side ? cd + n : cd, (int *)(cd + 2 * n) + side, 2,
+                    ex, g);
+        tri[2 * ci + side] = make_double2(ex ? 1.0 : 0.0, g);
+        steps = n;
+    }
+    for (int o = 16; o > 0; o >>= 1) steps += __shfl_xor_sync(FULL_MASK, steps, o);
+    if ((threadIdx.x & 31) == 0 && steps) atomicAdd(&info->shift_steps, steps);
+}
+
 // One warp per cluster {p..q} of node P (Alg. "Shifting the spectrum" inside a C-task).
 //  1. The cluster's extreme eigenvalues come refined from k_refine_ends.
-//  2. Candidates tau_l = lo_p - 100 eps |lo_p| and tau_r = hi_q + 100 eps |hi_q| (lanes 0, 1);
-//     a candidate exists when its factorization has no zero pivot and stays finite; of
+//  2. Candidates tau_l = lo_p - 100 eps |lo_p| and tau_r = hi_q + 100 eps |hi_q| (computed by
+//     k_shift_trials); a candidate exists when its factorization has no zero pivot and
+//     stays finite; of
 //     existing ones the smaller growth max|d+_i| is taken; it is accepted when
 //     max|d+_i| <= 8 spdiam(M_root).  Otherwise back off:
 //     tau_l - 2^(t-1) delta, tau_r + 2^(t-1) delta, delta = max(100 eps |lambda|, 1e-3 W)
@@ -514,7 +562,8 @@ __global__ void k_shift(int ncluster, const ClusterItem *__restrict__ clusters,
                         const BlkDesc *__restrict__ blks, const double *__restrict__ pool,
                         double *childpool, Node *child_nodes, double *child_tau, int *cnode,
                         int *active_list, const int *__restrict__ jloc, double *lo, double *hi,
-                        int max_tries, unsigned fault_mask, DevInfo *info) {
+                        int max_tries, unsigned fault_mask, const double2 *__restrict__ tri,
+                        DevInfo *info) {
     const int ci = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (ci >= ncluster) return;
@@ -539,17 +588,10 @@ __global__ void k_shift(int ncluster, const ClusterItem *__restrict__ clusters,
     const double delta = fmax(100.0 * kEps * fmax(fabs(Lp), fabs(Hq)), 1e-3 * W);
     const double thresh = 8.0 * B.spdiam;
     const bool reject_all = (fault_mask & MR3_FAULT_SHIFT_REJECT) != 0;
-    int *K = (int *)cdll; // int2 per element: .x lane-0 candidate, .y lane-1 candidate
-    bool ex = false;
-    double g = INFINITY;
-    if (lane < 2) {
-        double tau = lane == 0 ? tau_l0 : tau_r0;
-        if (lane == 0 && (fault_mask & MR3_FAULT_NAN_SHIFT)) tau = NAN;
-        trial_shift(n, pd, pdll, tau, true, lane == 0 ? cd : cdl, K + lane, 2, ex, g);
-        steps += n;
-    }
-    const int e0 = __shfl_sync(FULL_MASK, (int)ex, 0), e1 = __shfl_sync(FULL_MASK, (int)ex, 1);
-    const double g0 = __shfl_sync(FULL_MASK, g, 0), g1 = __shfl_sync(FULL_MASK, g, 1);
+    int *K = (int *)cdll; // int2 per element: .x candidate tau_l, .y candidate tau_r
+    const double2 t0 = tri[2 * ci], t1 = tri[2 * ci + 1];
+    const int e0 = t0.x != 0.0, e1 = t1.x != 0.0;
+    const double g0 = t0.y, g1 = t1.y;
     int win = -1;     // 0/1: stored candidate of try 0; 2: recompute needed
     double tau = 0.0; // the winner's shift
     bool untested = false;
@@ -687,13 +729,17 @@ void launch_shift(int ncluster, const ClusterItem *clusters, const long long *cl
                   const Node *nodes, const BlkDesc *blks, const double *pool, double *childpool,
                   Node *child_nodes, double *child_tau, int *cnode, int *active_list,
                   const int *jloc, double *lo, double *hi, int max_tries, unsigned fault_mask,
-                  DevInfo *info, cudaStream_t s) {
+                  double2 *tri, DevInfo *info, cudaStream_t s) {
     if (ncluster <= 0) return;
-    const int wpb = 1; // one warp per block: spread the serial trial sweeps over the SMs
+    // a block of 64 threads (32 clusters) keeps the trial warps spread over the SMs
+    k_shift_trials<<<(unsigned)((2ll * ncluster + 63) / 64), 64, 0, s>>>(
+        ncluster, clusters, cluster_rep, nodes, blks, pool, childpool, lo, hi, fault_mask, tri,
+        info);
+    const int wpb = 1; // one warp per block: spread the serial back-off sweeps over the SMs
     k_shift<<<(ncluster + wpb - 1) / wpb, 32 * wpb, 0, s>>>(ncluster, clusters, cluster_rep, nodes,
                                                            blks, pool, childpool, child_nodes,
                                                            child_tau, cnode, active_list, jloc, lo,
-                                                           hi, max_tries, fault_mask, info);
+                                                           hi, max_tries, fault_mask, tri, info);
 }
 
 // ------------------------------------------------------------------ output order

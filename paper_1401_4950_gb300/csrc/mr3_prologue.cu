@@ -1,7 +1,7 @@
 // mr3_prologue.cu -- everything before the representation tree is traversed:
 // splitting into irreducible blocks (Sec. 3.2.1), Gershgorin intervals (App. B,
 // Alg. Gershgorin), selection of the requested eigenpairs (App. A ranges), and the root
-// representation M_root = T - mu I with its random perturbation (Alg. MRRR lines 1-2).
+// representation M_root = T - mu I with its random perturbation (Alg. MRRR).
 #include <float.h>
 #include "mr3_kernels.h"
 #include "mr3_df.cuh"
@@ -418,12 +418,16 @@ void launch_assign_columns(int nmat, MatDesc *mats, BlkDesc *blks, int range, cu
 
 // ------------------------------------------------------------------ root representation
 
-// L D L^T = T - mu I by the homogeneous three-term recurrence (one dependent FMA per
-// step); the pivots d_i = p_i / p_{i-1} are divided off the critical path.  Reports
-// whether all pivots have the sign of a definite factorization (want_pos: positive) and
-// the largest |d_i| (element growth).
+// L D L^T = T - mu I by the homogeneous three-term recurrence
+//   p_i = (alpha_i - mu) p_{i-1} - beta_{i-1}^2 p_{i-2},   d_i = p_i / p_{i-1},
+// one dependent FMA per step: the unscaled p_i go to P[i] and the power-of-two rescale
+// applied after step i to K[i * kstride], so that the pivots can be divided out later in
+// parallel.  Reports whether every pivot has the sign of a definite factorization
+// (want_pos: positive; sign(d_i) = sign(p_i) xor sign(p_{i-1})) and the largest |d_i|
+// (element growth, a division only when the running maximum may grow).
 __device__ void factor_root(int n, const double *__restrict__ d, const double *__restrict__ e,
-                            double mu, double *piv, bool want_pos, bool &definite, double &growth) {
+                            double mu, double *P, int *K, int kstride, bool want_pos,
+                            bool &definite, double &growth) {
     double pm2 = 0.0, pm1 = 1.0;
     bool ok = true;
     double g = 0.0;
@@ -432,16 +436,19 @@ __device__ void factor_root(int n, const double *__restrict__ d, const double *_
         double q = 0.0;
         if (i > 0) { const double b = __ldg(e + i - 1); q = (b * b) * pm2; }
         double p = fma(ai, pm1, -q);
-        const double pv = p / pm1;
-        piv[i] = pv;
-        if (!(want_pos ? (pv > 0.0) : (pv < 0.0)) || !is_finite(pv)) ok = false;
-        g = fmax(g, fabs(pv));
+        P[i] = p;
+        const int neg = sign_bit(p) ^ sign_bit(pm1);
+        if ((want_pos ? neg : !neg) || is_zero(p) || !is_finite(p)) ok = false;
+        if (fabs(p) > g * fabs(pm1)) g = fmax(g, fabs(p / pm1));
+        int k = 0;
         const int ex = biased_exp(p);
         if (!is_zero(p) && (unsigned)(ex - (1023 - 200)) > 400u) {
-            const double s = pow2i(1023 - ex);
+            k = 1023 - ex;
+            const double s = pow2i(k);
             p *= s;
             pm1 *= s;
         }
+        K[(size_t)i * kstride] = k;
         pm2 = pm1;
         pm1 = p;
     }
@@ -456,7 +463,8 @@ __device__ void factor_root(int n, const double *__restrict__ d, const double *_
 // the smaller element growth wins, ties to the left; if neither is definite delta doubles
 // (at most 10 tries, then mu = gl - spdiam/8 which is always definite).  (3) The chosen
 // factorization's primary data d, l are perturbed by relative amounts xi u, xi = 8 eps,
-// u uniform in (-1, 1) from SplitMix64 (Alg. MRRR line 2), and dl, dll are derived.
+// u uniform in (-1, 1) from SplitMix64 (Alg. MRRR, perturbation of the root), and dl, dll
+// are derived.
 __global__ void k_root(int nblk, BlkDesc *blks, const double *__restrict__ D,
                        const double *__restrict__ E, double *pool0, float *f32,
                        unsigned long long seed) {
@@ -499,20 +507,24 @@ __global__ void k_root(int nblk, BlkDesc *blks, const double *__restrict__ D,
     if (!(dL > 0.0)) dL = kSafmin;
     if (!(dR > 0.0)) dR = kSafmin;
     double *reg0 = pool0 + B.rep, *reg1 = reg0 + n, *reg2 = reg0 + 2 * n;
+    int *K = (int *)reg2; // int2 per index: rescale exponents of the two candidates
     double mu = 0.0;
     const double *src = reg0;
+    int kofs = 0;
     bool found = false;
     for (int tr = 0; tr < 10 && !found; ++tr) {
         const double muL = L1 - dL, muR = Hn + dR;
         bool ok = false;
         double g = 0.0;
-        if (lane < 2) factor_root(n, d, e, lane == 0 ? muL : muR, lane == 0 ? reg0 : reg1, lane == 0, ok, g);
+        if (lane < 2)
+            factor_root(n, d, e, lane == 0 ? muL : muR, lane == 0 ? reg0 : reg1, K + lane, 2,
+                        lane == 0, ok, g);
         const int ok0 = __shfl_sync(FULL_MASK, (int)ok, 0), ok1 = __shfl_sync(FULL_MASK, (int)ok, 1);
         const double g0 = __shfl_sync(FULL_MASK, g, 0), g1 = __shfl_sync(FULL_MASK, g, 1);
         if (ok0 || ok1) {
             found = true;
-            if (ok0 && (!ok1 || g0 <= g1)) { mu = muL; src = reg0; }
-            else { mu = muR; src = reg1; }
+            if (ok0 && (!ok1 || g0 <= g1)) { mu = muL; src = reg0; kofs = 0; }
+            else { mu = muR; src = reg1; kofs = 1; }
         } else {
             dL *= 2.0;
             dR *= 2.0;
@@ -522,15 +534,30 @@ __global__ void k_root(int nblk, BlkDesc *blks, const double *__restrict__ D,
         mu = B.gl - 0.125 * B.spdiam - kSafmin;
         bool ok;
         double g;
-        if (lane == 0) factor_root(n, d, e, mu, reg0, true, ok, g);
+        if (lane == 0) factor_root(n, d, e, mu, reg0, K, 2, true, ok, g);
         src = reg0;
+        kofs = 0;
     }
     __syncwarp();
     const double xi = 8.0 * kEps;
     float4 *rdf = (float4 *)(reg0 + rep_df_offset(n));
     bool dfok = true;
-    for (int i = lane; i < n; i += 32) {
-        const double pv = src[i];
+    // pivots d_i = p_i / (p_{i-1} 2^k_{i-1}), by chunks of 32 (the previous chunk's last p
+    // and exponent carried in registers: the chunk's writes reuse the slots it read)
+    double carry_p = 1.0;
+    int carry_k = 0;
+    for (int base = 0; base < n; base += 32) {
+        const int i = base + lane;
+        const double pi = (i < n) ? src[i] : 1.0;
+        const int ki = (i < n) ? K[2 * i + kofs] : 0;
+        double pp = __shfl_up_sync(FULL_MASK, pi, 1);
+        int kp = __shfl_up_sync(FULL_MASK, ki, 1);
+        if (lane == 0) { pp = carry_p; kp = carry_k; }
+        carry_p = __shfl_sync(FULL_MASK, pi, 31);
+        carry_k = __shfl_sync(FULL_MASK, ki, 31);
+        __syncwarp();
+        if (i >= n) continue;
+        const double pv = (pi / pp) * pow2i(-kp);
         const unsigned long long ctr = 2ull * (unsigned long long)(B.roff + i);
         const double dp = pv * (1.0 + xi * splitmix_pm1(seed, ctr));
         double dl = 0.0, dll = 0.0;
@@ -547,6 +574,7 @@ __global__ void k_root(int nblk, BlkDesc *blks, const double *__restrict__ D,
         rdf[i] = make_float4(a.h, a.l, bb.h, bb.l);
         dfok &= df_safe(dp) && df_safe(dll);
     }
+    __syncwarp();
     dfok = __all_sync(FULL_MASK, dfok);
     __syncwarp();
     build_prefix(n, reg0);

@@ -11,7 +11,10 @@ namespace mr3 {
 // A team of kTeam lanes finishes one singleton; a warp holds kTeams teams.  Lanes 0 and 1
 // of a team run the two serial recurrences of a twisted factorization, after which all
 // lanes of the team share the element-wise work (twist index, solve, normalisation).
-constexpr int kTeam = 8;
+#ifndef MR3_RQI_TEAM
+#define MR3_RQI_TEAM 8
+#endif
+constexpr int kTeam = MR3_RQI_TEAM;
 constexpr int kTeams = 32 / kTeam;
 constexpr int kScratchPerIndex = 5 * kTeams; // doubles per index per warp slot
 
@@ -313,15 +316,31 @@ __global__ void __launch_bounds__(32) k_rqi(int nsingle, const SingleItem *__res
             // a correction at the rounding noise of the factorization cannot improve lam
             if (nofault && fabs(rqc) <= tol_noise * fabs(lam)) { done = true; continue; }
             if (it_n >= max_rqi) capped = true;
-            // bisection to full accuracy (every lane of the team, identically), then one
-            // more Getvec
-            for (int kk = 0; kk < 2100; ++kk) {
-                const double wd = h - l;
-                if (!(wd > fmax(4.0 * kEps * fmax(fabs(l), fabs(h)), 4.0 * kSafmin))) break;
-                const double mid = l + 0.5 * wd;
-                if (!(mid > l && mid < h)) break;
-                if (k == 0) steps += n;
-                if (negcount_ldl(n, d, dll, mid) < j) l = mid; else h = mid;
+            // bisection to full accuracy, as a multisection over the team's lanes (lane k
+            // counts at the (k+1)-th of kTeam interior points; the team ballot of
+            // "count < j" picks the part holding lambda_j), then one more Getvec
+            {
+                const unsigned tmask = (kTeam == 32) ? FULL_MASK : (((1u << kTeam) - 1u) << tbase);
+                for (int kk = 0; kk < 2100; ++kk) {
+                    const double wd = h - l;
+                    if (!(wd > fmax(4.0 * kEps * fmax(fabs(l), fabs(h)), 4.0 * kSafmin))) break;
+                    const double x = l + (k + 1) * (wd / (kTeam + 1));
+                    if (__ballot_sync(tmask, !(x > l && x < h)) & tmask) {
+                        // no representable interior points left: plain bisection
+                        const double mid = l + 0.5 * wd;
+                        if (!(mid > l && mid < h)) break;
+                        if (k == 0) steps += n;
+                        if (negcount_ldl(n, d, dll, mid) < j) l = mid; else h = mid;
+                        continue;
+                    }
+                    steps += n;
+                    const unsigned bal = __ballot_sync(tmask, negcount_ldl(n, d, dll, x) < j) & tmask;
+                    const int t = __popc(bal);
+                    const double xl = __shfl_sync(tmask, x, tbase + (t > 0 ? t - 1 : 0));
+                    const double xh = __shfl_sync(tmask, x, tbase + (t < kTeam ? t : kTeam - 1));
+                    if (t > 0) l = xl;
+                    if (t < kTeam) h = xh;
+                }
             }
             lam = l + 0.5 * (h - l);
             r = -1;

@@ -108,7 +108,7 @@ int lanes_auto(long long nactive, int tpe) {
         while (L * 2 <= tpe && L < 32) L *= 2;
         return L;
     }
-    const long long target = 152ll * 32 * 12;
+    const long long target = 152ll * 32 * 48;
     int L = 1;
     while (L < 32 && (long long)(2 * L) * nactive <= target) L *= 2;
     return L;
@@ -221,10 +221,11 @@ int solve_static(MatDesc &M, const double *d, const double *e, int range, double
         Node *next_nodes = ar.take<Node>(hc.ncluster, end);
         double *tau = ar.take<double>(hc.ncluster, end);
         int *next_active = ar.take<int>(hc.nactive, end);
+        double2 *tri = ar.take<double2>(2 * (size_t)hc.ncluster, end);
         SFULL(ar);
-        launch_refine_ends(hc.ncluster, clusters, cur_nodes, blks, cur_pool, jloc, lo, hi, dinfo, s);
+        launch_refine_ends(hc.ncluster, clusters, cur_nodes, blks, cur_pool, jloc, lo, hi, tri, dinfo, s);
         launch_shift(hc.ncluster, clusters, crep, cur_nodes, blks, cur_pool, next_pool, next_nodes,
-                     tau, cnode, next_active, jloc, lo, hi, max_tries, fault_mask, dinfo, s);
+                     tau, cnode, next_active, jloc, lo, hi, max_tries, fault_mask, tri, dinfo, s);
         launch_bisect(hc.nactive, next_active, lanes_auto(hc.nactive, tpe), (int)ncols, cnode,
                       next_nodes, blks, next_pool, jloc, lo, hi, rtol, tau, dinfo, s);
         cur_pool = next_pool;
