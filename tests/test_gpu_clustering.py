@@ -1,0 +1,52 @@
+"""Structure of the representation tree against the clustering the thesis prints
+(tests/golden/clustering_rho.txt: Ch. 5 Table tab:clustering and Table
+tab:clusteringdouble).  rho = largest cluster / n; rho = 1/n means no cluster at all.
+
+The binary64 rows were measured with LAPACK's DSTEMR, whose root representation and
+interval refinement differ in detail from this solver's; the comparison allows 0.15
+absolute.  The mixed-precision rows are structural (no cluster, or only the Wilkinson
+pairs) and are matched exactly."""
+import os
+
+import numpy as np
+import pytest
+
+import testmats as tm
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _rows():
+    out = []
+    for line in open(os.path.join(HERE, "golden", "clustering_rho.txt")):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        fam, n, tree, rho = line.split()
+        out.append((fam, int(n), tree, float(rho)))
+    return out
+
+
+def _matrix(fam, n):
+    if fam == "wilkinson":
+        return tm.make(fam, n + 1)  # the thesis' Wilkinson matrices have odd order n + 1
+    return tm.make(fam, n)
+
+
+@pytest.mark.parametrize("fam,n,tree,rho", _rows())
+def test_clustering_matches_thesis(cuda, fam, n, tree, rho):
+    import torch
+    import paper_1401_4950_gb300 as mr3
+    d, e = _matrix(fam, n)
+    dt, et = torch.tensor(d, device="cuda"), torch.tensor(e, device="cuda")
+    prec = mr3.FP64 if tree == "fp64" else mr3.DD
+    _, _, info = mr3.stemr(dt, et, opts=mr3.make_opts(prec=prec))
+    torch.cuda.synchronize()
+    nn = len(d)
+    ours = max(info["largest_cluster"], 1) / nn
+    if tree == "fp64":
+        assert abs(ours - rho) <= 0.15, (ours, rho)
+    else:
+        assert round(ours * n) == round(rho * n), (ours, rho)
