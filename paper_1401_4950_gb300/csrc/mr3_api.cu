@@ -56,12 +56,12 @@ int lanes_for(long long nactive, const Opts &o) {
     return L;
 }
 
-// Warp slots (one warp each) for an RQI launch: one per rqi_singles_per_slot()
-// singletons, within a scratch budget of cap_bytes.
-long long rqi_slots(long long nsingle, int nmax, long long cap_bytes) {
-    const int per = rqi_singles_per_slot();
+// Warp slots (one warp each) for an RQI launch with the given team size: one per
+// rqi_singles_per_slot(team) singletons, within a scratch budget of cap_bytes.
+long long rqi_slots(long long nsingle, int nmax, long long cap_bytes, int team) {
+    const int per = rqi_singles_per_slot(team);
     const long long want = (nsingle + per - 1) / per;
-    const long long per_slot = (long long)rqi_scratch_per_index() * nmax * (long long)sizeof(double);
+    const long long per_slot = (long long)rqi_scratch_per_index(team) * nmax * (long long)sizeof(double);
     const long long cap = std::max<long long>(152, cap_bytes / per_slot);
     return std::min(want, cap);
 }
@@ -284,23 +284,25 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
     double *cur_pool = pool0, *cur_lo = pool0_lo;
     int ncur = nblk;
     double *scratch = nullptr;
-    long long scratch_slots = 0;
+    size_t scratch_len = 0; // doubles
     const long long scratch_cap_bytes = 2ll << 30; // RQI scratch budget per launch
     int status = 0;
     auto run_singles = [&](int level, const LevelCounters &hc) -> int {
+        const int team = dd ? 0 : rqi_team(hc.nsingle);
         long long slots = dd ? rqi_dd_threads(hc.nsingle, nmax, 2 * scratch_cap_bytes)
-                             : rqi_slots(hc.nsingle, nmax, scratch_cap_bytes);
-        const size_t per_slot = dd ? (size_t)4 * nmax : (size_t)rqi_scratch_per_index() * nmax;
-        if (slots > scratch_slots) {
+                             : rqi_slots(hc.nsingle, nmax, scratch_cap_bytes, team);
+        const size_t per_slot = dd ? (size_t)4 * nmax : (size_t)rqi_scratch_per_index(team) * nmax;
+        const size_t need = (size_t)slots * per_slot;
+        if (need > scratch_len) {
             if (scratch) cudaFreeAsync(scratch, side); // after the side stream's last use
             void *p = nullptr;
-            if (cudaMallocAsync(&p, (size_t)slots * per_slot * sizeof(double), s) != cudaSuccess) {
+            if (cudaMallocAsync(&p, need * sizeof(double), s) != cudaSuccess) {
                 cudaGetLastError();
                 scratch = nullptr;
                 return MR3_EOOM;
             }
             scratch = (double *)p;
-            scratch_slots = slots;
+            scratch_len = need;
         }
         cudaEvent_t ready = guard.make();
         cudaEventRecord(ready, s);
@@ -313,7 +315,7 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
         else
             launch_rqi(hc.nsingle, singles2[level & 1], cur_nodes, blks, dmats, cur_pool, jloc, lo,
                        hi, gapl, gapr, d, e, w, Z, scratch, (int)slots, nmax, o.max_rqi,
-                       o.fault_mask, work, dinfo, side);
+                       o.fault_mask, work, dinfo, team, side);
         prof.end(tq, 4, 1, side);
         cudaEvent_t done = guard.make();
         cudaEventRecord(done, side);
@@ -344,23 +346,25 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
         Node *next_nodes = ws.get<Node>(hc.ncluster);
         double *tau = ws.get<double>(hc.ncluster);
         double2 *tri = ws.get<double2>(2 * (size_t)hc.ncluster);
+        char *shift_ws = ws.get<char>(shift_scratch_bytes(hc.ncluster, o.max_tries));
         int *next_active = ws.get<int>(hc.nactive);
         CKW(ws);
         tk = prof.begin();
         launch_refine_ends(hc.ncluster, clusters, cur_nodes, blks, cur_pool, jloc, lo, hi, tri, dinfo, s);
         launch_shift(hc.ncluster, clusters, crep, cur_nodes, blks, cur_pool, next_pool,
                      next_nodes, tau, cnode, next_active, jloc, lo, hi, o.max_tries, o.fault_mask,
-                     tri, dinfo, s);
+                     tri, shift_ws, dinfo, s);
         if (dd)
             launch_shift_dd(hc.ncluster, clusters, crep, cur_nodes, blks, cur_pool, cur_lo, next_pool,
                             next_lo, next_nodes, tau, dinfo, s);
-        prof.end(tk, 5, dd ? 5 : 4); // refine_ends x2, shift trials, shift (+ double-double recompute)
+        prof.end(tk, 5, dd ? 9 : 8); // refine_ends x2, six shift kernels (+ double-double recompute)
         tk = prof.begin();
         launch_bisect(hc.nactive, next_active, lanes_for(hc.nactive, o), (int)ncols, cnode,
                       next_nodes, blks, next_pool, jloc, lo, hi, rtol, tau, dinfo, s);
         prof.end(tk, 6, 1);
         ws.release(next_active);
         ws.release(tri);
+        ws.release(shift_ws);
         // return representations no longer read: older levels whose RQI has finished
         for (auto &pnd : pending) {
             if (pnd.done) cudaStreamWaitEvent(s, pnd.done, 0);

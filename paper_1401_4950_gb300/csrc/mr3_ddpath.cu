@@ -10,9 +10,10 @@
 //  * each child representation is recomputed in double-double from its parent with the
 //    shift tau the binary64 shift kernel selected -- k_shift_dd.  dstqds keeps the
 //    off-diagonal of L D L^T, so dl+ = dl and dll+ = dl^2 / d+;
-//  * eigenvalues are approximated in binary64 on the leading words (the rounded copy M_x
-//    of Ch. 5, "Arithmetic used to approximate eigenvalues"), safe while
-//    (k_rr + k_bi) n eps_x <~ gaptol; the default gaptol is 1e-10;
+//  * eigenvalues are approximated on the leading words (the rounded copy M_x of Ch. 5,
+//    "Arithmetic used to approximate eigenvalues"), safe while (k_rr + k_bi) n eps_x <~
+//    gaptol, the default gaptol being 1e-10: in double-float down to its accuracy, then
+//    in binary64;
 //  * singletons get their eigenvectors from a twisted factorization and Rayleigh-quotient
 //    iteration in double-double, stopped when the local residual is below
 //    gap eps_x sqrt(n) (the relaxed criterion of Ch. 5, k_rs = 1) or the correction is at
@@ -83,7 +84,8 @@ __global__ void k_root_dd(int nblk, BlkDesc *blks, const double *__restrict__ D,
         pm2 = pm1;
         pm1 = p;
     }
-    blks[b].dfok = 0; // the bisection counts on the leading words in binary64
+    // the double-float copy written by the binary64 root stays a valid x-bit copy of this
+    // representation (the two differ by a few units of 2^-53, far below 2^-47)
 }
 
 // ---------------------------------------------------------------- child representations
@@ -129,7 +131,6 @@ __global__ void k_shift_dd(int ncluster, const ClusterItem *__restrict__ cluster
         }
         cp = c;
     }
-    child_nodes[ci].dfok = 0;
     atomicAdd(&info->shift_steps, (unsigned long long)n);
 }
 

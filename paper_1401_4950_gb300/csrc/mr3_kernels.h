@@ -58,12 +58,15 @@ void launch_classify(int nnode, const Node *nodes, const BlkDesc *blks, const do
 void launch_refine_ends(int ncluster, const ClusterItem *clusters, const Node *nodes,
                         const BlkDesc *blks, const double *pool, const int *jloc, double *lo,
                         double *hi, double2 *carry, DevInfo *info, cudaStream_t s);
-// tri: scratch of 2 ncluster double2 (existence and growth of the first two candidates).
+// tri: scratch of 2 ncluster double2 (existence and growth of the first two candidates);
+// ws: shift_scratch_bytes(ncluster, max_tries) bytes (decisions, back-off results, queues).
 void launch_shift(int ncluster, const ClusterItem *clusters, const long long *cluster_rep,
                   const Node *nodes, const BlkDesc *blks, const double *pool, double *childpool,
                   Node *child_nodes, double *child_tau, int *cnode, int *active_list,
                   const int *jloc, double *lo, double *hi, int max_tries, unsigned fault_mask,
-                  double2 *tri, DevInfo *info, cudaStream_t s);
+                  double2 *tri, void *ws, DevInfo *info, cudaStream_t s);
+// Bytes of the ws scratch launch_shift needs for ncluster clusters.
+size_t shift_scratch_bytes(int ncluster, int max_tries);
 // Ascending eigenvalues: running-maximum fix for single-block matrices, flags for the rest.
 void launch_order_flags(int nmat, const MatDesc *mats, double *w, int *flags, cudaStream_t s);
 // Sort the m eigenpairs of matrix mi (temporaries: m values, n x m entries, m ints).
@@ -76,12 +79,13 @@ void launch_rqi(int nsingle, const SingleItem *singles, const Node *nodes, const
                 const double *hi, const double *gapl, const double *gapr, const double *d,
                 const double *e, double *w, double *Z, double *scratch, int nslots, int nmax,
                 int max_rqi, unsigned fault_mask, int *work_counter, DevInfo *info,
-                cudaStream_t s);
+                int team, cudaStream_t s);
 
-// Scratch doubles per index per warp slot of the singleton kernel, and singletons a warp
-// slot holds at a time.
-int rqi_scratch_per_index();
-int rqi_singles_per_slot();
+// Team size (lanes per singleton, 2 or 8) for a launch of nsingle singletons; scratch doubles
+// per index per warp slot, and singletons a warp slot holds at a time, for that team size.
+int rqi_team(long long nsingle);
+int rqi_scratch_per_index(int team);
+int rqi_singles_per_slot(int team);
 
 // ---- double-double representation tree (mr3_ddpath.cu, opts->prec = MR3_DD).  A pool
 // holding representations keeps the leading words in the binary64 layout and the low

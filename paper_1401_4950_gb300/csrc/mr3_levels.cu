@@ -127,10 +127,22 @@ __global__ void k_bisect2(int ngroups, const int *__restrict__ list, int L, int 
             }
         }
     }
-    // ---- multisection
+    // ---- multisection.  Double-float counts while the interval is wider than their
+    // accuracy (64 n 2^-47 relative); below that the interval is widened by the
+    // double-float error bound and the bisection goes on in binary64.
     const double atol = 4.0 * kSafmin;
+    const double kap = 32.0 * n * 0x1p-47;
     bool used_df = false;
+    bool df_phase = N.dfok != 0;
     for (int sweep = 0; sweep < 400; ++sweep) {
+        if (active && df_phase && h - l <= 2.0 * kap * fmax(fabs(l), fabs(h))) {
+            if (used_df) {
+                l -= kap * fabs(l);
+                h += kap * fabs(h);
+            }
+            df_phase = false;
+            used_df = false;
+        }
         const double w = h - l;
         bool done = !active || !(w > fmax(rtol * fmax(fabs(l), fabs(h)), atol));
         const double x = l + (k + 1) * (w / (L + 1));
@@ -139,8 +151,12 @@ __global__ void k_bisect2(int ngroups, const int *__restrict__ list, int L, int 
         if (__all_sync(0xffffffffu, done)) break;
         int cnt = 0;
         if (!done) {
-            used_df |= (N.dfok && df_safe(x));
-            cnt = node_count(N, n, rep, x);
+            if (df_phase) {
+                used_df |= df_safe(x);
+                cnt = node_count(N, n, rep, x);
+            } else {
+                cnt = negcount_ldl(n, rep, rep + 2 * n, x);
+            }
             steps += n;
         }
         const unsigned bal = __ballot_sync(0xffffffffu, cnt < j);
@@ -155,7 +171,6 @@ __global__ void k_bisect2(int ngroups, const int *__restrict__ list, int L, int 
     const bool grp_df = (__ballot_sync(0xffffffffu, used_df) & gmask) != 0;
     if (active && k == 0) {
         if (grp_df) {
-            const double kap = 32.0 * n * 0x1p-47;
             l -= kap * fabs(l);
             h += kap * fabs(h);
         }
@@ -545,24 +560,183 @@ __global__ void k_shift_trials(int ncluster, const ClusterItem *__restrict__ clu
     if ((threadIdx.x & 31) == 0 && steps) atomicAdd(&info->shift_steps, steps);
 }
 
+// The shift decision of one cluster: its tau, which stored factorization holds the child
+// (0: tau_l's, 1: tau_r's, 2: recomputed), and whether it was accepted untested.
+struct ShiftDecision {
+    double tau;
+    int win;
+    int untested;
+};
+
+// Candidates of a cluster: tau_l0, tau_r0 at 100 eps from the refined ends, the back-off
+// unit delta = max(100 eps |lambda|, 1e-3 W) and the growth threshold 8 spdiam(M_root).
+struct ShiftSetup {
+    double tau_l0, tau_r0, delta, thresh;
+};
+__device__ __forceinline__ ShiftSetup shift_setup(const ClusterItem &C, const BlkDesc &B,
+                                                  const double *__restrict__ lo,
+                                                  const double *__restrict__ hi) {
+    const double Lp = lo[C.c0], Hq = hi[C.c1];
+    ShiftSetup S;
+    S.tau_l0 = Lp - MR3_TAU_OFFSET * kEps * fabs(Lp);
+    S.tau_r0 = Hq + MR3_TAU_OFFSET * kEps * fabs(Hq);
+    S.delta = fmax(100.0 * kEps * fmax(fabs(Lp), fabs(Hq)), 1e-3 * (Hq - Lp));
+    S.thresh = 8.0 * B.spdiam;
+    return S;
+}
+
+__host__ __device__ __forceinline__ int ladder_width(int max_tries) {
+    return 2 * (max(2, min(max_tries, 16)) - 1);
+}
+
+// One thread per cluster: take the better existing first candidate if its growth passes,
+// else queue the cluster for the back-off ladder.
+__global__ void k_shift_select(int ncluster, const ClusterItem *__restrict__ clusters,
+                               const Node *__restrict__ nodes, const BlkDesc *__restrict__ blks,
+                               const double *__restrict__ lo, const double *__restrict__ hi,
+                               unsigned fault_mask, const double2 *__restrict__ tri,
+                               ShiftDecision *dec, int *ladder, int *counts) {
+    const int ci = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ci >= ncluster) return;
+    const ClusterItem C = clusters[ci];
+    const BlkDesc B = blks[nodes[C.node].blk];
+    const ShiftSetup S = shift_setup(C, B, lo, hi);
+    const double2 t0 = tri[2 * ci], t1 = tri[2 * ci + 1];
+    const bool e0 = t0.x != 0.0, e1 = t1.x != 0.0;
+    int sel = -1;
+    if (e0 && e1) sel = (t0.y <= t1.y) ? 0 : 1;
+    else if (e0) sel = 0;
+    else if (e1) sel = 1;
+    const bool reject_all = (fault_mask & MR3_FAULT_SHIFT_REJECT) != 0;
+    if (sel >= 0 && !reject_all && (sel == 0 ? t0.y : t1.y) <= S.thresh) {
+        dec[ci] = {sel == 0 ? S.tau_l0 : S.tau_r0, sel, 0};
+    } else {
+        dec[ci] = {0.0, -1, 0};
+        ladder[atomicAdd(counts, 1)] = ci;
+    }
+}
+
+// One lane per back-off candidate: tau_l0 - 2^(t-1) delta (even j) and
+// tau_r0 + 2^(t-1) delta (odd j), t = j / 2 + 1, for every queued cluster.
+__global__ void k_shift_ladder(int nslots, int max_tries, const ClusterItem *__restrict__ clusters,
+                               const Node *__restrict__ nodes, const BlkDesc *__restrict__ blks,
+                               const double *__restrict__ pool, const double *__restrict__ lo,
+                               const double *__restrict__ hi, const int *__restrict__ ladder,
+                               const int *__restrict__ counts, double2 *lad, DevInfo *info) {
+    const int NL = ladder_width(max_tries);
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int li = (int)(gid / NL), j = (int)(gid % NL);
+    unsigned long long steps = 0;
+    if (li < nslots && li < counts[0]) {
+        const int ci = ladder[li];
+        const ClusterItem C = clusters[ci];
+        const Node P = nodes[C.node];
+        const BlkDesc B = blks[P.blk];
+        const int n = B.n;
+        const ShiftSetup S = shift_setup(C, B, lo, hi);
+        const double off = ldexp(S.delta, j / 2);
+        const double tau = (j & 1) ? S.tau_r0 + off : S.tau_l0 - off;
+        const double *pd = pool + P.rep;
+        bool ex = false;
+        double g = INFINITY;
+        trial_shift(n, pd, pd + 2 * n, tau, false, nullptr, nullptr, 0, ex, g);
+        lad[(long long)li * NL + j] = make_double2(ex ? 1.0 : 0.0, g);
+        steps = n;
+    }
+    for (int o = 16; o > 0; o >>= 1) steps += __shfl_xor_sync(FULL_MASK, steps, o);
+    if ((threadIdx.x & 31) == 0 && steps) atomicAdd(&info->shift_steps, steps);
+}
+
+// One thread per queued cluster: the first back-off step t whose better existing candidate
+// passes the growth test wins (recomputed); else the least growth over every candidate,
+// the first two included, accepted untested.
+__global__ void k_shift_pick(int nslots, int max_tries, unsigned fault_mask,
+                             const ClusterItem *__restrict__ clusters,
+                             const Node *__restrict__ nodes, const BlkDesc *__restrict__ blks,
+                             const double *__restrict__ lo, const double *__restrict__ hi,
+                             const double2 *__restrict__ tri, const int *__restrict__ ladder,
+                             int *counts, const double2 *__restrict__ lad, ShiftDecision *dec,
+                             int *recomp) {
+    const int li = blockIdx.x * blockDim.x + threadIdx.x;
+    if (li >= nslots || li >= counts[0]) return;
+    const int NL = ladder_width(max_tries);
+    const int ci = ladder[li];
+    const ClusterItem C = clusters[ci];
+    const ShiftSetup S = shift_setup(C, blks[nodes[C.node].blk], lo, hi);
+    const bool reject_all = (fault_mask & MR3_FAULT_SHIFT_REJECT) != 0;
+    const double2 *L = lad + (long long)li * NL;
+    auto tau_of = [&](int j) {
+        const double off = ldexp(S.delta, j / 2);
+        return (j & 1) ? S.tau_r0 + off : S.tau_l0 - off;
+    };
+    ShiftDecision D = {0.0, -1, 0};
+    for (int jL = 0; jL < NL; jL += 2) {
+        const bool exL = L[jL].x != 0.0, exR = L[jL + 1].x != 0.0;
+        int sel = -1;
+        if (exL && exR) sel = (L[jL].y <= L[jL + 1].y) ? jL : jL + 1;
+        else if (exL) sel = jL;
+        else if (exR) sel = jL + 1;
+        if (sel >= 0 && !reject_all && L[sel].y <= S.thresh) { D = {tau_of(sel), 2, 0}; break; }
+    }
+    if (D.win < 0) {
+        const double2 t0 = tri[2 * ci], t1 = tri[2 * ci + 1];
+        const bool e0 = t0.x != 0.0, e1 = t1.x != 0.0;
+        double gb = INFINITY;
+        int jb = -1;
+        for (int j = 0; j < NL; ++j)
+            if (L[j].x != 0.0 && L[j].y < gb) { gb = L[j].y; jb = j; }
+        if (e0 && t0.y <= gb && (!e1 || t0.y <= t1.y)) D = {S.tau_l0, 0, 1};
+        else if (e1 && t1.y <= gb) D = {S.tau_r0, 1, 1};
+        else if (jb >= 0) D = {tau_of(jb), 2, 1};
+        else D = {S.tau_l0, 0, 1}; // nothing exists: keep the first candidate (flagged)
+    }
+    dec[ci] = D;
+    if (D.win == 2) recomp[atomicAdd(counts + 1, 1)] = ci;
+}
+
+// One lane per cluster whose winner is a back-off candidate: its factorization again,
+// stored like a first candidate on the tau_l side.
+__global__ void k_shift_recompute(int nslots, const ClusterItem *__restrict__ clusters,
+                                  const long long *__restrict__ cluster_rep,
+                                  const Node *__restrict__ nodes, const BlkDesc *__restrict__ blks,
+                                  const double *__restrict__ pool, double *childpool,
+                                  const int *__restrict__ recomp, const int *__restrict__ counts,
+                                  const ShiftDecision *__restrict__ dec, DevInfo *info) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long steps = 0;
+    if (r < nslots && r < counts[1]) {
+        const int ci = recomp[r];
+        const Node P = nodes[clusters[ci].node];
+        const int n = blks[P.blk].n;
+        const double *pd = pool + P.rep;
+        double *cd = childpool + cluster_rep[ci];
+        bool ex;
+        double g;
+        trial_shift(n, pd, pd + 2 * n, dec[ci].tau, true, cd, (int *)(cd + 2 * n), 2, ex, g);
+        steps = n;
+    }
+    for (int o = 16; o > 0; o >>= 1) steps += __shfl_xor_sync(FULL_MASK, steps, o);
+    if ((threadIdx.x & 31) == 0 && steps) atomicAdd(&info->shift_steps, steps);
+}
+
 // One warp per cluster {p..q} of node P (Alg. "Shifting the spectrum" inside a C-task).
 //  1. The cluster's extreme eigenvalues come refined from k_refine_ends.
-//  2. Candidates tau_l = lo_p - 100 eps |lo_p| and tau_r = hi_q + 100 eps |hi_q| (computed by
-//     k_shift_trials); a candidate exists when its factorization has no zero pivot and
-//     stays finite; of
+//  2. Candidates tau_l = lo_p - 100 eps |lo_p| and tau_r = hi_q + 100 eps |hi_q| (k_shift_trials,
+//     one lane each; k_shift_select); a candidate exists when its factorization has no
+//     zero pivot and stays finite; of
 //     existing ones the smaller growth max|d+_i| is taken; it is accepted when
 //     max|d+_i| <= 8 spdiam(M_root).  Otherwise back off:
 //     tau_l - 2^(t-1) delta, tau_r + 2^(t-1) delta, delta = max(100 eps |lambda|, 1e-3 W)
-//     (W the cluster width), t = 1 .. max_tries-1, evaluated in parallel; the first t
-//     with an accepted candidate wins, else the least growth overall (counted untested).
+//     (W the cluster width), t = 1 .. max_tries-1, one lane per candidate (k_shift_ladder,
+//     k_shift_pick); the first t with an accepted candidate wins and is recomputed
+//     (k_shift_recompute), else the least growth overall (counted untested).
 //  3. The winner's c_i give the child: d+_i = c_i / c_{i-1}, l+_i = dl_i / d+_i,
 //     dl+_i = d+_i l+_i, dll+_i = dl+_i l+_i, converted in place by chunks of 32.
 __global__ void k_shift(int ncluster, const ClusterItem *__restrict__ clusters,
                         const long long *__restrict__ cluster_rep, const Node *__restrict__ nodes,
                         const BlkDesc *__restrict__ blks, const double *__restrict__ pool,
                         double *childpool, Node *child_nodes, double *child_tau, int *cnode,
-                        int *active_list, const int *__restrict__ jloc, double *lo, double *hi,
-                        int max_tries, unsigned fault_mask, const double2 *__restrict__ tri,
+                        int *active_list, const ShiftDecision *__restrict__ dec,
                         DevInfo *info) {
     const int ci = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -571,92 +745,16 @@ __global__ void k_shift(int ncluster, const ClusterItem *__restrict__ clusters,
     const Node P = nodes[C.node];
     const BlkDesc B = blks[P.blk];
     const int n = B.n;
-    const double *pd = pool + P.rep, *pdl = pd + n, *pdll = pd + 2 * n;
+    const double *pdl = pool + P.rep + n;
     double *cd = childpool + cluster_rep[ci], *cdl = cd + n, *cdll = cd + 2 * n;
     const int p = C.c0, q = C.c1;
-    unsigned long long steps = 0;
 
-    // ---- 1. the cluster ends were refined by k_refine_ends
-    const double L = lo[p], H = hi[q];
-    const double Lp = L;
-    const double Hq = H;
-
-    // ---- 2. shift candidates
-    const double tau_l0 = Lp - MR3_TAU_OFFSET * kEps * fabs(Lp);
-    const double tau_r0 = Hq + MR3_TAU_OFFSET * kEps * fabs(Hq);
-    const double W = Hq - Lp;
-    const double delta = fmax(100.0 * kEps * fmax(fabs(Lp), fabs(Hq)), 1e-3 * W);
-    const double thresh = 8.0 * B.spdiam;
-    const bool reject_all = (fault_mask & MR3_FAULT_SHIFT_REJECT) != 0;
-    int *K = (int *)cdll; // int2 per element: .x candidate tau_l, .y candidate tau_r
-    const double2 t0 = tri[2 * ci], t1 = tri[2 * ci + 1];
-    const int e0 = t0.x != 0.0, e1 = t1.x != 0.0;
-    const double g0 = t0.y, g1 = t1.y;
-    int win = -1;     // 0/1: stored candidate of try 0; 2: recompute needed
-    double tau = 0.0; // the winner's shift
-    bool untested = false;
-    {
-        int sel = -1;
-        if (e0 && e1) sel = (g0 <= g1) ? 0 : 1;
-        else if (e0) sel = 0;
-        else if (e1) sel = 1;
-        if (sel >= 0 && !reject_all && (sel == 0 ? g0 : g1) <= thresh) {
-            win = sel;
-            tau = sel == 0 ? tau_l0 : tau_r0;
-        }
-    }
-    if (win < 0) {
-        // back-off ladder: lane 2(t-1)+side for t = 1..T-1
-        const int T = max(2, min(max_tries, 16));
-        const int t = (lane >> 1) + 1;
-        const int side = lane & 1;
-        bool ex2 = false;
-        double g2 = INFINITY, tau2 = NAN;
-        if (t < T) {
-            const double off = ldexp(delta, t - 1);
-            tau2 = side ? tau_r0 + off : tau_l0 - off;
-            trial_shift(n, pd, pdll, tau2, false, nullptr, nullptr, 0, ex2, g2);
-            steps += n;
-        }
-        const bool pass = ex2 && !reject_all && g2 <= thresh;
-        // first t whose better existing candidate passes
-        int best_t = -1;
-        for (int tt = 1; tt < T; ++tt) {
-            const int lL = 2 * (tt - 1), lR = lL + 1;
-            const int exL = __shfl_sync(FULL_MASK, (int)ex2, lL), exR = __shfl_sync(FULL_MASK, (int)ex2, lR);
-            const double gL = __shfl_sync(FULL_MASK, g2, lL), gR = __shfl_sync(FULL_MASK, g2, lR);
-            int s = -1;
-            if (exL && exR) s = (gL <= gR) ? lL : lR;
-            else if (exL) s = lL;
-            else if (exR) s = lR;
-            if (s >= 0 && __shfl_sync(FULL_MASK, (int)pass, s)) { best_t = s; break; }
-        }
-        if (best_t >= 0) {
-            tau = __shfl_sync(FULL_MASK, tau2, best_t);
-        } else {
-            // least element growth over every computed candidate (try 0 included)
-            double gb = g2;
-            int lb = lane;
-            for (int o = 16; o > 0; o >>= 1) {
-                const double og = __shfl_xor_sync(FULL_MASK, gb, o);
-                const int ol = __shfl_xor_sync(FULL_MASK, lb, o);
-                if (og < gb || (og == gb && ol < lb)) { gb = og; lb = ol; }
-            }
-            const double tb = __shfl_sync(FULL_MASK, tau2, lb);
-            if (e0 && g0 <= gb && (!e1 || g0 <= g1)) { win = 0; tau = tau_l0; }
-            else if (e1 && g1 <= gb) { win = 1; tau = tau_r0; }
-            else if (isfinite(gb)) { tau = tb; }
-            else { win = 0; tau = tau_l0; } // nothing exists: keep try 0 (flagged untested)
-            untested = true;
-        }
-        if (win < 0) {
-            win = 2;
-            bool dummy_e;
-            double dummy_g;
-            if (lane == 0) { trial_shift(n, pd, pdll, tau, true, cd, K, 2, dummy_e, dummy_g); steps += n; }
-        }
-    }
-    __syncwarp();
+    // ---- 1-2. ends refined (k_refine_ends), shift chosen (k_shift_trials .. k_shift_pick)
+    const ShiftDecision D = dec[ci];
+    const double tau = D.tau;
+    const int win = D.win;
+    const bool untested = D.untested != 0;
+    int *K = (int *)cdll; // int2 per element: .x candidate tau_l (or recomputed), .y tau_r
 
     // ---- 3. convert the stored c_i into the child representation (in place), with its
     // double-float copy for the bisection
@@ -721,25 +819,45 @@ __global__ void k_shift(int ncluster, const ClusterItem *__restrict__ clusters,
         atomicAdd(&info->new_rrr, 1);
         if (untested) { atomicAdd(&info->untested, 1); atomicAdd(&info->status[MR3_SUNTESTED_RRR], 1); }
     }
-    for (int o = 16; o > 0; o >>= 1) steps += __shfl_xor_sync(FULL_MASK, steps, o);
-    if (lane == 0 && steps) atomicAdd(&info->shift_steps, steps);
+}
+
+size_t shift_scratch_bytes(int ncluster, int max_tries) {
+    const size_t nc = (size_t)std::max(ncluster, 1);
+    return nc * sizeof(ShiftDecision) + nc * (size_t)ladder_width(max_tries) * sizeof(double2) +
+           (2 * nc + 2) * sizeof(int);
 }
 
 void launch_shift(int ncluster, const ClusterItem *clusters, const long long *cluster_rep,
                   const Node *nodes, const BlkDesc *blks, const double *pool, double *childpool,
                   Node *child_nodes, double *child_tau, int *cnode, int *active_list,
                   const int *jloc, double *lo, double *hi, int max_tries, unsigned fault_mask,
-                  double2 *tri, DevInfo *info, cudaStream_t s) {
+                  double2 *tri, void *ws, DevInfo *info, cudaStream_t s) {
+    (void)jloc;
     if (ncluster <= 0) return;
-    // a block of 64 threads (32 clusters) keeps the trial warps spread over the SMs
+    const int NL = ladder_width(max_tries);
+    ShiftDecision *dec = (ShiftDecision *)ws;
+    double2 *lad = (double2 *)(dec + ncluster);
+    int *ladder = (int *)(lad + (size_t)ncluster * NL);
+    int *recomp = ladder + ncluster;
+    int *counts = recomp + ncluster;
+    cudaMemsetAsync(counts, 0, 2 * sizeof(int), s);
+    // first candidates, one lane each (blocks of 64 threads keep the warps spread)
     k_shift_trials<<<(unsigned)((2ll * ncluster + 63) / 64), 64, 0, s>>>(
         ncluster, clusters, cluster_rep, nodes, blks, pool, childpool, lo, hi, fault_mask, tri,
         info);
-    const int wpb = 1; // one warp per block: spread the serial back-off sweeps over the SMs
-    k_shift<<<(ncluster + wpb - 1) / wpb, 32 * wpb, 0, s>>>(ncluster, clusters, cluster_rep, nodes,
-                                                           blks, pool, childpool, child_nodes,
-                                                           child_tau, cnode, active_list, jloc, lo,
-                                                           hi, max_tries, fault_mask, tri, info);
+    const unsigned cb = (unsigned)((ncluster + 127) / 128);
+    k_shift_select<<<cb, 128, 0, s>>>(ncluster, clusters, nodes, blks, lo, hi, fault_mask, tri,
+                                      dec, ladder, counts);
+    // back-off ladder for the queued clusters (threads past the queue's length return)
+    k_shift_ladder<<<(unsigned)(((long long)ncluster * NL + 63) / 64), 64, 0, s>>>(
+        ncluster, max_tries, clusters, nodes, blks, pool, lo, hi, ladder, counts, lad, info);
+    k_shift_pick<<<cb, 128, 0, s>>>(ncluster, max_tries, fault_mask, clusters, nodes, blks, lo, hi,
+                                    tri, ladder, counts, lad, dec, recomp);
+    k_shift_recompute<<<(unsigned)((ncluster + 63) / 64), 64, 0, s>>>(
+        ncluster, clusters, cluster_rep, nodes, blks, pool, childpool, recomp, counts, dec, info);
+    // conversion to the child representations, one warp per cluster
+    k_shift<<<ncluster, 32, 0, s>>>(ncluster, clusters, cluster_rep, nodes, blks, pool, childpool,
+                                    child_nodes, child_tau, cnode, active_list, dec, info);
 }
 
 // ------------------------------------------------------------------ output order

@@ -8,25 +8,25 @@ namespace mr3 {
 
 #define FULL_MASK 0xffffffffu
 
-// A team of kTeam lanes finishes one singleton; a warp holds kTeams teams.  Lanes 0 and 1
+// A team of TEAM lanes finishes one singleton; a warp holds 32 / TEAM teams.  Lanes 0 and 1
 // of a team run the two serial recurrences of a twisted factorization, after which all
 // lanes of the team share the element-wise work (twist index, solve, normalisation).
-#ifndef MR3_RQI_TEAM
-#define MR3_RQI_TEAM 8
-#endif
-constexpr int kTeam = MR3_RQI_TEAM;
-constexpr int kTeams = 32 / kTeam;
-constexpr int kScratchPerIndex = 5 * kTeams; // doubles per index per warp slot
+// Teams of 8 keep a singleton's element-wise passes short (levels with few singletons are
+// latency bound); teams of 2 fill 4x more lanes of every binary64 instruction in the
+// recurrences, which wins when singletons far outnumber the resident warps (the binary64
+// pipe costs the same per warp instruction whatever the number of active lanes).
+constexpr int kScratchPerSingleton = 5; // doubles per index per singleton
 
 // Scratch of one team: per index five values (a_i, c_{i-1}, h_i, d_i f_{i+1}, and the two
 // scale exponents as an int2), interleaved with the other teams of the warp.
-struct Scratch {
+template <int TEAMS> struct Scratch {
+    static constexpr int kSPI = kScratchPerSingleton * TEAMS; // doubles per index per warp slot
     double *base; // warp slot base + team
-    __device__ __forceinline__ double &A(int i) const { return base[(size_t)i * kScratchPerIndex]; }
-    __device__ __forceinline__ double &C(int i) const { return base[(size_t)i * kScratchPerIndex + kTeams]; }
-    __device__ __forceinline__ double &H(int i) const { return base[(size_t)i * kScratchPerIndex + 2 * kTeams]; }
-    __device__ __forceinline__ double &Q(int i) const { return base[(size_t)i * kScratchPerIndex + 3 * kTeams]; }
-    __device__ __forceinline__ int2 &E(int i) const { return *(int2 *)(base + (size_t)i * kScratchPerIndex + 4 * kTeams); }
+    __device__ __forceinline__ double &A(int i) const { return base[(size_t)i * kSPI]; }
+    __device__ __forceinline__ double &C(int i) const { return base[(size_t)i * kSPI + TEAMS]; }
+    __device__ __forceinline__ double &H(int i) const { return base[(size_t)i * kSPI + 2 * TEAMS]; }
+    __device__ __forceinline__ double &Q(int i) const { return base[(size_t)i * kSPI + 3 * TEAMS]; }
+    __device__ __forceinline__ int2 &E(int i) const { return *(int2 *)(base + (size_t)i * kSPI + 4 * TEAMS); }
 };
 
 // Rescale (x, y) by 2^k so that |x| is near 1 when x leaves [2^-200, 2^200]; returns k.
@@ -59,22 +59,22 @@ __device__ __forceinline__ float log2abs(double x) {
     return (float)(ex - 1023) + __log2f(mant);
 }
 
-// Reductions over the kTeam lanes of a team (all 32 lanes call them together).
-__device__ __forceinline__ double team_sum(double v) {
-    for (int o = kTeam / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, kTeam);
+// Reductions over the TEAM lanes of a team (all 32 lanes call them together).
+template <int TEAM> __device__ __forceinline__ double team_sum(double v) {
+    for (int o = TEAM / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, TEAM);
     return v;
 }
-__device__ __forceinline__ void team_argmin(float &key, int &idx) {
-    for (int o = kTeam / 2; o > 0; o >>= 1) {
-        const float k2 = __shfl_xor_sync(0xffffffffu, key, o, kTeam);
-        const int i2 = __shfl_xor_sync(0xffffffffu, idx, o, kTeam);
+template <int TEAM> __device__ __forceinline__ void team_argmin(float &key, int &idx) {
+    for (int o = TEAM / 2; o > 0; o >>= 1) {
+        const float k2 = __shfl_xor_sync(0xffffffffu, key, o, TEAM);
+        const int i2 = __shfl_xor_sync(0xffffffffu, idx, o, TEAM);
         if (k2 < key || (k2 == key && i2 < idx)) { key = k2; idx = i2; }
     }
 }
-__device__ __forceinline__ void team_argmax_bits(long long &b, int &idx) {
-    for (int o = kTeam / 2; o > 0; o >>= 1) {
-        const long long b2 = __shfl_xor_sync(0xffffffffu, b, o, kTeam);
-        const int i2 = __shfl_xor_sync(0xffffffffu, idx, o, kTeam);
+template <int TEAM> __device__ __forceinline__ void team_argmax_bits(long long &b, int &idx) {
+    for (int o = TEAM / 2; o > 0; o >>= 1) {
+        const long long b2 = __shfl_xor_sync(0xffffffffu, b, o, TEAM);
+        const int i2 = __shfl_xor_sync(0xffffffffu, idx, o, TEAM);
         if (b2 > b || (b2 == b && i2 < idx)) { b = b2; idx = i2; }
     }
 }
@@ -108,6 +108,7 @@ __device__ __forceinline__ void team_argmax_bits(long long &b, int &idx) {
 // diag(d+_0..d+_{r-1}, gamma_r, omega-_{r+1}..omega-_{n-1}).  The eigenvalue returned is the
 // Rayleigh quotient of z with respect to the input T (accuracy remark 5, Sec. 3.1.2), which
 // removes the bias of the root's random perturbation.
+template <int TEAM>
 __global__ void __launch_bounds__(32) k_rqi(int nsingle, const SingleItem *__restrict__ singles,
                                             const Node *__restrict__ nodes,
                                             const BlkDesc *__restrict__ blks,
@@ -123,11 +124,12 @@ __global__ void __launch_bounds__(32) k_rqi(int nsingle, const SingleItem *__res
                                             double *scratch, int nmax, int max_rqi,
                                             unsigned fault_mask, int *work_counter,
                                             DevInfo *info) {
+    constexpr int kTeam = TEAM, kTeams = 32 / TEAM;
     const int lane = threadIdx.x & 31;
     const int team = lane / kTeam, k = lane % kTeam, tbase = team * kTeam;
     const int slot = blockIdx.x;
-    Scratch S;
-    S.base = scratch + (size_t)slot * kScratchPerIndex * (size_t)nmax + team;
+    Scratch<kTeams> S;
+    S.base = scratch + (size_t)slot * Scratch<kTeams>::kSPI * (size_t)nmax + team;
     unsigned long long steps = 0, iters = 0;
     int itmax = 0, nfb = 0, ncap = 0;
     for (;;) {
@@ -237,6 +239,7 @@ __global__ void __launch_bounds__(32) k_rqi(int nsingle, const SingleItem *__res
                     best = log2abs(c_last) - log2abs(cprev_last);
                     if (!(best == best)) best = 3.0e38f;
                 }
+#pragma unroll 4
                 for (int i = k; i < n - 1; i += kTeam) {
                     const double ci = S.C(i), hv = S.H(i);
                     const double num = fma(S.A(i), hv, ci * S.Q(i));
@@ -244,7 +247,7 @@ __global__ void __launch_bounds__(32) k_rqi(int nsingle, const SingleItem *__res
                     if (key < best || (key == best && i < rr)) { best = key; rr = i; }
                 }
             }
-            team_argmin(best, rr);
+            team_argmin<kTeam>(best, rr);
             double gamma = 1.0;
             int negc = 0;
             if (!done) {
@@ -272,6 +275,7 @@ __global__ void __launch_bounds__(32) k_rqi(int nsingle, const SingleItem *__res
                 const int rg = (r < n - 1) ? S.E(r).y : 0;
                 const double qmr = Qm[r], iqmr = iQm[r];
                 const int qer = Qe[r];
+#pragma unroll 4
                 for (int i = k; i < n; i += kTeam) {
                     double z;
                     if (i < r) {
@@ -290,8 +294,8 @@ __global__ void __launch_bounds__(32) k_rqi(int nsingle, const SingleItem *__res
                 }
                 steps += (unsigned long long)((n + kTeam - 1) / kTeam);
             }
-            ss = team_sum(ss);
-            team_argmax_bits(zb, zi_max);
+            ss = team_sum<kTeam>(ss);
+            team_argmax_bits<kTeam>(zb, zi_max);
             if (done) continue;
             // ---- acceptance (uniform within the team)
             nrm2 = ss;
@@ -351,17 +355,19 @@ __global__ void __launch_bounds__(32) k_rqi(int nsingle, const SingleItem *__res
         if (active) {
             const double zsign = (zc[imax] < 0.0) ? -1.0 : 1.0;
             const double scale = zsign / sqrt(nrm2);
+#pragma unroll 4
             for (int i = k; i < n; i += kTeam) zc[i] *= scale;
         }
         __syncwarp();
         if (active) {
+#pragma unroll 4
             for (int i = k; i < n; i += kTeam) {
                 const double zi = zc[i];
                 rq = fma(__ldg(td + i) * zi, zi, rq);
                 if (i + 1 < n) rq = fma(2.0 * __ldg(te + i) * zi, zc[i + 1], rq);
             }
         }
-        rq = team_sum(rq);
+        rq = team_sum<kTeam>(rq);
         if (active && k == 0) {
             w[c] = rq;
             iters += it_n;
@@ -393,17 +399,26 @@ void launch_rqi(int nsingle, const SingleItem *singles, const Node *nodes, const
                 const double *hi, const double *gapl, const double *gapr, const double *d,
                 const double *e, double *w, double *Z, double *scratch, int nslots, int nmax,
                 int max_rqi, unsigned fault_mask, int *work_counter, DevInfo *info,
-                cudaStream_t s) {
+                int team, cudaStream_t s) {
     if (nsingle <= 0) return;
-    const int want = (nsingle + kTeams - 1) / kTeams;
+    const int per = 32 / team;
+    const int want = (nsingle + per - 1) / per;
     const int nblocks = want < nslots ? want : nslots;
     cudaMemsetAsync(work_counter, 0, sizeof(int), s);
-    k_rqi<<<nblocks, 32, 0, s>>>(nsingle, singles, nodes, blks, mats, pool, jloc, lo, hi, gapl,
-                                 gapr, d, e, w, Z, scratch, nmax, max_rqi, fault_mask,
-                                 work_counter, info);
+    if (team == 2)
+        k_rqi<2><<<nblocks, 32, 0, s>>>(nsingle, singles, nodes, blks, mats, pool, jloc, lo, hi,
+                                        gapl, gapr, d, e, w, Z, scratch, nmax, max_rqi,
+                                        fault_mask, work_counter, info);
+    else
+        k_rqi<8><<<nblocks, 32, 0, s>>>(nsingle, singles, nodes, blks, mats, pool, jloc, lo, hi,
+                                        gapl, gapr, d, e, w, Z, scratch, nmax, max_rqi,
+                                        fault_mask, work_counter, info);
 }
 
-int rqi_scratch_per_index() { return kScratchPerIndex; }
-int rqi_singles_per_slot() { return kTeams; }
+// Teams of 2 once the singletons clearly outnumber what the resident warps hold with teams
+// of 8 (about 17 warps per SM at this kernel's register count, 4 singletons each).
+int rqi_team(long long nsingle) { return nsingle > 32768 ? 2 : 8; }
+int rqi_scratch_per_index(int team) { return kScratchPerSingleton * (32 / team); }
+int rqi_singles_per_slot(int team) { return 32 / team; }
 
 } // namespace mr3

@@ -180,11 +180,12 @@ int solve_static(MatDesc &M, const double *d, const double *e, int range, double
     LevelCounters *ctr = ar.low<LevelCounters>(1);
     int *work = ar.low<int>(1);
     // RQI scratch: up to a quarter of the array, at most one warp slot per 4 singletons
-    const size_t slot_bytes = (size_t)rqi_scratch_per_index() * n * sizeof(double);
-    const long long want_slots = (mtotal + rqi_singles_per_slot() - 1) / rqi_singles_per_slot();
+    const int team = 8; // lanes per singleton (the latency-bound choice for one matrix)
+    const size_t slot_bytes = (size_t)rqi_scratch_per_index(team) * n * sizeof(double);
+    const long long want_slots = (mtotal + rqi_singles_per_slot(team) - 1) / rqi_singles_per_slot(team);
     const long long cap_slots = std::max<long long>(1, (MR3_STATIC_SCRATCH_BYTES / 4) / slot_bytes);
     const int slots = (int)std::min(want_slots, cap_slots);
-    double *rqi_scratch = ar.low<double>((size_t)slots * rqi_scratch_per_index() * n);
+    double *rqi_scratch = ar.low<double>((size_t)slots * rqi_scratch_per_index(team) * n);
     SFULL(ar);
     ar.seal_fixed();
     SCK(cudaMemsetAsync(cnode, 0xff, sizeof(int) * ncols, s));
@@ -213,7 +214,7 @@ int solve_static(MatDesc &M, const double *d, const double *e, int range, double
         if (hc.nsingle > 0)
             launch_rqi(hc.nsingle, singles, cur_nodes, blks, dmats, cur_pool, jloc, lo, hi, gapl,
                        gapr, d, e, w, Z, rqi_scratch, slots, (int)n, max_rqi, fault_mask, work,
-                       dinfo, s);
+                       dinfo, team, s);
         if (hc.ncluster == 0) break;
         const int end = (level + 1) & 1;
         ar.reset_end(end);
@@ -222,10 +223,12 @@ int solve_static(MatDesc &M, const double *d, const double *e, int range, double
         double *tau = ar.take<double>(hc.ncluster, end);
         int *next_active = ar.take<int>(hc.nactive, end);
         double2 *tri = ar.take<double2>(2 * (size_t)hc.ncluster, end);
+        char *shift_ws = ar.take<char>(shift_scratch_bytes(hc.ncluster, max_tries), end);
         SFULL(ar);
         launch_refine_ends(hc.ncluster, clusters, cur_nodes, blks, cur_pool, jloc, lo, hi, tri, dinfo, s);
         launch_shift(hc.ncluster, clusters, crep, cur_nodes, blks, cur_pool, next_pool, next_nodes,
-                     tau, cnode, next_active, jloc, lo, hi, max_tries, fault_mask, tri, dinfo, s);
+                     tau, cnode, next_active, jloc, lo, hi, max_tries, fault_mask, tri, shift_ws,
+                     dinfo, s);
         launch_bisect(hc.nactive, next_active, lanes_auto(hc.nactive, tpe), (int)ncols, cnode,
                       next_nodes, blks, next_pool, jloc, lo, hi, rtol, tau, dinfo, s);
         cur_pool = next_pool;
@@ -242,7 +245,7 @@ int solve_static(MatDesc &M, const double *d, const double *e, int range, double
             if (hc.nsingle > 0)
                 launch_rqi(hc.nsingle, singles, cur_nodes, blks, dmats, cur_pool, jloc, lo, hi,
                            gapl, gapr, d, e, w, Z, rqi_scratch, slots, (int)n, max_rqi,
-                           fault_mask, work, dinfo, s);
+                           fault_mask, work, dinfo, team, s);
             break;
         }
     }
