@@ -8,7 +8,8 @@
 //   TwoSum (Knuth, TAOCP vol. 2), Fast2Sum (Dekker 1971), TwoProd via FMA;
 //   double-word + double-word "accurate" addition, double-word x double-word and
 //   double-word x binary64 multiplication (Joldes, Muller and Popescu, ACM TOMS 44(2),
-//   2017); division by one Newton-style correction of the binary64 quotient (Dekker 1971).
+//   2017); reciprocal by one Newton step on the binary64 reciprocal, division as a product
+//   with it.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -81,15 +82,20 @@ __device__ __forceinline__ ddouble dd_prod(double a, double b) {
     return {p, __fma_rn(a, b, -p)};
 }
 
-// x / y: q1 = x.h / y.h, remainder x - q1 y in double-word, q2 = remainder / y.h.
-__device__ __forceinline__ ddouble dd_div(ddouble x, ddouble y) {
-    const double q1 = __ddiv_rn(x.h, y.h);
-    const ddouble r = dd_sub(x, dd_mul_d(y, q1));
-    const double q2 = __ddiv_rn(r.h, y.h);
-    ddouble q;
-    dd_fast_two_sum(q1, q2, q.h, q.l);
-    return q;
+// 1 / y: the binary64 reciprocal r0 of y.h, corrected by one Newton step carried in
+// double-word, r = r0 + r0 (1 - y r0), with the residual 1 - y r0 formed from the exact
+// product (relative error of r about 2^-104).
+__device__ __forceinline__ ddouble dd_rcp(ddouble y) {
+    const double r0 = __drcp_rn(y.h);
+    const ddouble p = dd_mul_d(y, r0);
+    const double e = __dsub_rn(__dsub_rn(1.0, p.h), p.l);
+    ddouble r;
+    dd_fast_two_sum(r0, __dmul_rn(r0, e), r.h, r.l);
+    return r;
 }
+
+// x / y as x (1 / y): one binary64 reciprocal instead of two binary64 divisions.
+__device__ __forceinline__ ddouble dd_div(ddouble x, ddouble y) { return dd_mul(x, dd_rcp(y)); }
 
 // x * 2^k exactly (k within the normal range of both words)
 __device__ __forceinline__ ddouble dd_scale(ddouble x, double pow2) {

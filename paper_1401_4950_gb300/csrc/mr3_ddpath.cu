@@ -22,6 +22,7 @@
 #include <algorithm>
 #include "mr3_kernels.h"
 #include "mr3_dd.cuh"
+#include "mr3_df.cuh"
 
 namespace mr3 {
 
@@ -58,6 +59,8 @@ __global__ void k_root_dd(int nblk, BlkDesc *blks, const double *__restrict__ D,
     double *h0 = pool0 + B.rep, *l0 = pool0_lo + B.rep;
     const double mu = B.mu, xi = 8.0 * kEps;
     ddouble pm2 = dd_make(0.0), pm1 = dd_make(1.0);
+    float4 *rdf = (float4 *)(h0 + rep_df_offset(n));
+    bool dfok = true;
     for (int i = 0; i < n; ++i) {
         ddouble a;
         dd_two_sum(__ldg(d + i), -mu, a.h, a.l);
@@ -79,13 +82,16 @@ __global__ void k_root_dd(int nblk, BlkDesc *blks, const double *__restrict__ D,
         h0[i] = dp.h;          l0[i] = dp.l;
         h0[n + i] = dl.h;      l0[n + i] = dl.l;
         h0[2 * n + i] = dll.h; l0[2 * n + i] = dll.l;
+        const dfloat fa = df_from(dp.h), fc = df_from(dll.h);
+        rdf[i] = make_float4(fa.h, fa.l, fc.h, fc.l);
+        dfok &= df_safe(dp.h) && df_safe(dll.h) && is_finite(dp.h) && is_finite(dll.h);
         const double s = rescale_factor(p.h);
         if (s != 1.0) { p = dd_scale(p, s); pm1 = dd_scale(pm1, s); }
         pm2 = pm1;
         pm1 = p;
     }
-    // the double-float copy written by the binary64 root stays a valid x-bit copy of this
-    // representation (the two differ by a few units of 2^-53, far below 2^-47)
+    // the bisection's double-float copy is rewritten from these leading words
+    blks[b].dfok = dfok ? 1 : 0;
 }
 
 // ---------------------------------------------------------------- child representations
@@ -108,6 +114,8 @@ __global__ void k_shift_dd(int ncluster, const ClusterItem *__restrict__ cluster
     const double *ph = pool + P.rep, *pl = pool_lo + P.rep;
     double *ch = childpool + cluster_rep[ci], *cl = childpool_lo + cluster_rep[ci];
     const double tau = child_tau[ci];
+    float4 *cdf = (float4 *)(ch + rep_df_offset(n));
+    bool dfok = true;
     ddouble a = dd_make(-tau), cp = dd_make(1.0);
     for (int i = 0; i < n; ++i) {
         ddouble c = dd_add(dd_mul(dd_load(ph, pl, i), cp), a);
@@ -115,6 +123,7 @@ __global__ void k_shift_dd(int ncluster, const ClusterItem *__restrict__ cluster
         const ddouble dp = dd_div(c, cp);
         ch[i] = dp.h;
         cl[i] = dp.l;
+        double dllh = 0.0;
         if (i < n - 1) {
             const ddouble dl = dd_load(ph, pl, n + i);
             const ddouble dllp = dd_div(dd_mul(dl, dl), dp);
@@ -122,6 +131,7 @@ __global__ void k_shift_dd(int ncluster, const ClusterItem *__restrict__ cluster
             cl[n + i] = dl.l;
             ch[2 * n + i] = dllp.h;
             cl[2 * n + i] = dllp.l;
+            dllh = dllp.h;
             a = dd_sub(dd_mul(dd_load(ph, pl, 2 * n + i), a), dd_mul_d(c, tau));
             const double s = rescale_factor(c.h);
             if (s != 1.0) { c = dd_scale(c, s); a = dd_scale(a, s); }
@@ -129,8 +139,13 @@ __global__ void k_shift_dd(int ncluster, const ClusterItem *__restrict__ cluster
             ch[n + i] = 0.0;     cl[n + i] = 0.0;
             ch[2 * n + i] = 0.0; cl[2 * n + i] = 0.0;
         }
+        // the bisection's double-float copy, rewritten from this child's leading words
+        const dfloat fa = df_from(dp.h), fc = df_from(dllh);
+        cdf[i] = make_float4(fa.h, fa.l, fc.h, fc.l);
+        dfok &= df_safe(dp.h) && df_safe(dllh) && is_finite(dp.h) && is_finite(dllh);
         cp = c;
     }
+    child_nodes[ci].dfok = dfok ? 1 : 0;
     atomicAdd(&info->shift_steps, (unsigned long long)n);
 }
 
@@ -202,19 +217,20 @@ __global__ void __launch_bounds__(128) k_rqi_dd(
         int it_n = 0, imax = 0;
         double nrm2 = 1.0;
         for (int guard = 0; guard < 64; ++guard) {
-            // ---- forward
+            // ---- forward (one reciprocal of d+_i serves l+_i and the next s)
             ddouble s = dd_neg(lam);
             int negc = 0;
             for (int i = 0; i < n - 1; ++i) {
                 ddouble dp = dd_add(dd_load(Rh, Rl, i), s);
                 if (is_zero(dp.h)) dp = dd_make(-0x1p-1000);
                 negc += dd_neg_sign(dp) ? 1 : 0;
-                const ddouble lp = dd_div(dd_load(Rh, Rl, n + i), dp);
+                const ddouble rdp = dd_rcp(dp);
+                const ddouble lp = dd_mul(dd_load(Rh, Rl, n + i), rdp);
                 S.at(i, 0) = lp.h;
                 S.at(i, 1) = lp.l;
                 S.at(i, 2) = s.h;
                 S.at(i, 3) = s.l;
-                s = dd_sub(dd_mul(dd_load(Rh, Rl, 2 * n + i), dd_div(s, dp)), lam);
+                s = dd_sub(dd_mul(dd_mul(dd_load(Rh, Rl, 2 * n + i), s), rdp), lam);
             }
             {
                 ddouble dp = dd_add(dd_load(Rh, Rl, n - 1), s);
@@ -229,10 +245,12 @@ __global__ void __launch_bounds__(128) k_rqi_dd(
             for (int i = n - 2; i >= 0; --i) {
                 ddouble rr = dd_add(dd_load(Rh, Rl, 2 * n + i), p);
                 if (is_zero(rr.h)) rr = dd_make(0x1p-1000);
-                const ddouble um = dd_div(dd_load(Rh, Rl, n + i), rr);
-                p = dd_sub(dd_mul(p, dd_div(dd_load(Rh, Rl, i), rr)), lam);
+                const ddouble rrr = dd_rcp(rr);
+                const ddouble um = dd_mul(dd_load(Rh, Rl, n + i), rrr);
+                const ddouble x = dd_mul(dd_mul(p, dd_load(Rh, Rl, i)), rrr); // p_i + lam
+                p = dd_sub(x, lam);
                 const ddouble si = {S.at(i, 2), S.at(i, 3)};
-                const ddouble g = dd_add(dd_add(si, p), lam);
+                const ddouble g = dd_add(si, x); // gamma_i = s_i + p_i + lam
                 S.at(i, 2) = um.h;
                 S.at(i, 3) = um.l;
                 if (fabs(g.h) < agmin) { agmin = fabs(g.h); gam = g; r = i; }
@@ -365,9 +383,12 @@ void launch_rqi_dd(int nsingle, const SingleItem *singles, const Node *nodes, co
                    long long nthreads, int max_rqi, unsigned fault_mask, DevInfo *info,
                    cudaStream_t s) {
     if (nsingle <= 0 || nthreads <= 0) return;
-    // scratch holds 4 nmax doubles for each of nthreads threads (a multiple of 128, or
-    // fewer than 128); the grid uses at most that many and loops over the singletons
-    const int bs = (int)std::min<long long>(128, nthreads);
+    // The kernel is bound by the binary64 pipe of the SMs it runs on: spread the singletons
+    // over all 152 SMs (blocks of ceil(nsingle / 152) threads, at most 128).  Scratch holds
+    // 4 nmax doubles for each of nthreads threads; the grid uses at most that many and loops
+    // over the singletons.
+    const long long per_sm = (nsingle + 151) / 152;
+    const int bs = (int)std::max<long long>(1, std::min<long long>({128, per_sm, nthreads}));
     const long long need = (nsingle + bs - 1) / bs;
     const unsigned nb = (unsigned)std::min<long long>(need, nthreads / bs);
     k_rqi_dd<<<nb, bs, 0, s>>>(nsingle, singles, nodes, blks, mats, pool, pool_lo, jloc, lo,

@@ -187,7 +187,8 @@ void launch_bisect(int ngroups, const int *list, int L, int mtotal, const int *c
                    cudaStream_t s) {
     if (ngroups <= 0) return;
     const long long threads = (long long)ngroups * L;
-    const int bs = 128;
+    // small launches in single-warp blocks, so that they spread over all SMs
+    const int bs = threads >= 152ll * 128 * 2 ? 128 : 32;
     k_bisect2<<<(unsigned)((threads + bs - 1) / bs), bs, 0, s>>>(ngroups, list, L, mtotal, cnode,
                                                                  nodes, blks, pool, jloc, lo, hi,
                                                                  rtol, tau_of_node, info);
@@ -473,12 +474,12 @@ void launch_refine_ends(int ncluster, const ClusterItem *clusters, const Node *n
     if (ncluster <= 0) return;
     // lanes per end: many ends -> fewer lanes (throughput), few ends -> more (latency)
     const long long ends = 2ll * ncluster;
-    const int bs = 64;
     for (int phase = 0; phase < 2; ++phase) {
         const long long cap = 152ll * 32 * (phase == 0 ? MR3_REFINE_WARPS_PER_SM : 2);
         int E = phase == 0 ? 4 : 2;
         while (E < 32 && ends * (2 * E) <= cap) E *= 2;
         const long long threads = ends * E;
+        const int bs = threads >= 152ll * 64 * 2 ? 64 : 32; // small launches spread over the SMs
         k_refine_ends<<<(unsigned)((threads + bs - 1) / bs), bs, 0, s>>>(
             ncluster, clusters, nodes, blks, pool, jloc, lo, hi, E, phase, carry, info);
     }

@@ -34,6 +34,10 @@ def test_dd_matches_oracle(cuda, kind, n):
     assert info["m"] == n
     # every family, the tight-pair ones included, within the 10 n eps gates
     check_eigenpairs(d, e, w, Z)
+    # the Rayleigh-quotient iteration converges from the bisection's intervals: a fallback
+    # to bisection is the exception (its intervals must bracket the double-double
+    # representation's eigenvalues)
+    assert info["bisect_fallbacks"] <= max(1, n // 100), info["bisect_fallbacks"]
 
 
 @pytest.mark.parametrize("kind,n", [("wilkinson", 1001), ("glued_wilkinson", 1000),
