@@ -18,6 +18,11 @@ namespace mr3 {
 #define MR3_REFINE_WARPS_PER_SM 8
 #endif
 
+// ... and to its binary64 phase: lanes per SM (the binary64 pipe is the limit there).
+#ifndef MR3_REFINE1_LANES_PER_SM
+#define MR3_REFINE1_LANES_PER_SM 128
+#endif
+
 #ifndef MR3_TAU_OFFSET
 #define MR3_TAU_OFFSET 100.0
 #endif
@@ -475,8 +480,9 @@ void launch_refine_ends(int ncluster, const ClusterItem *clusters, const Node *n
     // lanes per end: many ends -> fewer lanes (throughput), few ends -> more (latency)
     const long long ends = 2ll * ncluster;
     for (int phase = 0; phase < 2; ++phase) {
-        const long long cap = 152ll * 32 * (phase == 0 ? MR3_REFINE_WARPS_PER_SM : 2);
-        int E = phase == 0 ? 4 : 2;
+        const long long cap = phase == 0 ? 152ll * 32 * MR3_REFINE_WARPS_PER_SM
+                                         : 152ll * MR3_REFINE1_LANES_PER_SM;
+        int E = phase == 0 ? 4 : 1;
         while (E < 32 && ends * (2 * E) <= cap) E *= 2;
         const long long threads = ends * E;
         const int bs = threads >= 152ll * 64 * 2 ? 64 : 32; // small launches spread over the SMs
@@ -842,19 +848,19 @@ void launch_shift(int ncluster, const ClusterItem *clusters, const long long *cl
     int *recomp = ladder + ncluster;
     int *counts = recomp + ncluster;
     cudaMemsetAsync(counts, 0, 2 * sizeof(int), s);
-    // first candidates, one lane each (blocks of 64 threads keep the warps spread)
-    k_shift_trials<<<(unsigned)((2ll * ncluster + 63) / 64), 64, 0, s>>>(
+    // first candidates, one lane each (single-warp blocks keep the warps spread)
+    k_shift_trials<<<(unsigned)((2ll * ncluster + 31) / 32), 32, 0, s>>>(
         ncluster, clusters, cluster_rep, nodes, blks, pool, childpool, lo, hi, fault_mask, tri,
         info);
     const unsigned cb = (unsigned)((ncluster + 127) / 128);
     k_shift_select<<<cb, 128, 0, s>>>(ncluster, clusters, nodes, blks, lo, hi, fault_mask, tri,
                                       dec, ladder, counts);
     // back-off ladder for the queued clusters (threads past the queue's length return)
-    k_shift_ladder<<<(unsigned)(((long long)ncluster * NL + 63) / 64), 64, 0, s>>>(
+    k_shift_ladder<<<(unsigned)(((long long)ncluster * NL + 31) / 32), 32, 0, s>>>(
         ncluster, max_tries, clusters, nodes, blks, pool, lo, hi, ladder, counts, lad, info);
     k_shift_pick<<<cb, 128, 0, s>>>(ncluster, max_tries, fault_mask, clusters, nodes, blks, lo, hi,
                                     tri, ladder, counts, lad, dec, recomp);
-    k_shift_recompute<<<(unsigned)((ncluster + 63) / 64), 64, 0, s>>>(
+    k_shift_recompute<<<(unsigned)((ncluster + 31) / 32), 32, 0, s>>>(
         ncluster, clusters, cluster_rep, nodes, blks, pool, childpool, recomp, counts, dec, info);
     // conversion to the child representations, one warp per cluster
     k_shift<<<ncluster, 32, 0, s>>>(ncluster, clusters, cluster_rep, nodes, blks, pool, childpool,

@@ -284,3 +284,75 @@ def test_split_product_wide_dynamic_range(cuda):
     assert np.all(np.isfinite(dd)) and np.all(np.isfinite(de))
     assert np.max(np.abs(dd - rd)) <= 1e-11 * scale
     assert np.max(np.abs(de - re_)) <= 1e-11 * scale
+
+
+def test_backward_workload_eigenvalue_part_fd(cuda):
+    # the backward workload's matrix (n = 4096, uniform(-1, 1), seeds 501, 502), loss
+    # sum(g . lambda) with g ~ N(0, 1) (seed 503): central differences at h = 1e-6 along two
+    # random unit directions agree to 1e-6 of the gradient's norm (the difference quotient's
+    # own noise is ~sqrt(n) eps ||T|| / h ~ 1e-7 absolute, so a direction with a small
+    # derivative cannot be held to 1e-6 of itself).  Off-diagonals near zero almost split
+    # such a matrix, so some eigenvalue pairs sit at avoided crossings with gaps far below
+    # h, across which a single eigenvalue is not smooth at that step; the sum over such a
+    # group is, so g is made constant within groups closer than 1e-4.
+    n = 4096
+    d, e = tm.random_uniform(n, 501, 502)
+    g = tm.normal(503, n)
+    w, Z = _fwd(d, e)
+    wc = w.cpu().numpy()
+    for i in range(1, n):
+        if wc[i] - wc[i - 1] < 1e-4:
+            g[i] = g[i - 1]
+    dd, de = _bwd(w, Z, g=g)
+    gnorm = np.sqrt(dd @ dd + 0.5 * de @ de)  # dual norm of the unit directions below
+
+    def loss(dv, ev):
+        wv, _ = _fwd(dv, ev)
+        return float(g @ wv.cpu().numpy())
+
+    h = 1e-6
+    for k in range(2):
+        vd = tm.normal(505 + 2 * k, n)
+        ve = tm.normal(506 + 2 * k, n - 1)
+        nv = np.sqrt(vd @ vd + 2 * ve @ ve)
+        vd, ve = vd / nv, ve / nv
+        fd = (loss(d + h * vd, e + h * ve) - loss(d - h * vd, e - h * ve)) / (2 * h)
+        an = float(dd @ vd + de @ ve)
+        assert abs(fd - an) <= 1e-6 * gnorm, (fd, an, gnorm)
+
+
+def test_backward_full_loss_fd_n4096_double_double_forward(cuda):
+    # loss sum(g . lambda) + sum(G o Z) at n = 4096 on a matrix with gaps ~8/n, the forward
+    # through the double-double tree (eigenvectors accurate far below what h = 1e-6 can
+    # see): central differences along a random unit direction against the backward
+    import torch
+    import paper_1401_4950_gb300 as mr3
+    n = 4096
+    d, e = _separated(n, 61)
+    g = tm.normal(62, n)
+    G = tm.normal(63, n * n).reshape(n, n)
+    opts = mr3.make_opts(prec=mr3.DD)
+
+    def fwd(dv, ev):
+        w, Z, _ = mr3.stemr(torch.tensor(dv, device="cuda"), torch.tensor(ev, device="cuda"),
+                            opts=opts)
+        return w, Z
+
+    w0, Z0 = fwd(d, e)
+    dd, de = _bwd(w0, Z0, g=g, G=G)
+    Z0c = Z0.cpu().numpy()
+    Gt = torch.tensor(G, device="cuda")
+
+    def loss(dv, ev):
+        w, Z = fwd(dv, ev)
+        s = torch.sign(torch.einsum("ij,ij->j", Z, torch.tensor(Z0c, device="cuda")))
+        return float(torch.tensor(g, device="cuda") @ w + torch.sum(Gt * (Z * s[None, :])))
+
+    h = 1e-6
+    vd = tm.normal(64, n)
+    ve = tm.normal(65, n - 1)
+    nv = np.sqrt(vd @ vd + 2 * ve @ ve)
+    vd, ve = vd / nv, ve / nv
+    fd = (loss(d + h * vd, e + h * ve) - loss(d - h * vd, e - h * ve)) / (2 * h)
+    an = float(dd @ vd + de @ ve)
+    assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)
