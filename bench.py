@@ -1,9 +1,10 @@
 #!/usr/bin/env python3
 """Benchmark of the GB300 MRRR path: eigenpairs/s for all eigenpairs of n = 8192 FP64
 symmetric tridiagonals (one 1-2-1, one Wilkinson W+ and one uniform(-1,1) matrix per
-step), with a live roofline of the dominant kernel, the CPU oracle timed beside it, an
-end-to-end number through the host-buffer C-ABI call, and SM clocks sampled during the
-timed region.
+step, solved together by one mr3_stemr_batched call; --solver single times one mr3_stemr
+call per matrix), with a live roofline of the dominant kernel, the CPU oracle timed
+beside it, an end-to-end number (pinned host buffers copied in and out inside the timed
+region), and SM clocks sampled during the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mr3|reference] [--config c2]
 
@@ -211,13 +212,24 @@ def run_gpu(args, cfg, rank, world):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     opts = mr3.make_opts(profile=1)
     stream = torch.cuda.current_stream()
+    # the step's matrices packed for one mr3_stemr_batched call (d and e with the same
+    # offsets, the last e slot of each matrix unused)
+    sizes = [len(d) for _, d, _ in mats]
+    n_off = np.zeros(len(sizes) + 1, dtype=np.int64)
+    n_off[1:] = np.cumsum(sizes)
+    dcat_h = np.concatenate([np.asarray(d, dtype=np.float64) for _, d, _ in mats])
+    ecat_h = np.concatenate([np.r_[np.asarray(e, dtype=np.float64), 0.0] for _, _, e in mats])
+    dcat, ecat = torch.tensor(dcat_h, device=dev), torch.tensor(ecat_h, device=dev)
 
     def step():
-        infos = []
-        for _, d, e in dev_mats:
-            _, _, info = mr3.stemr(d, e, opts=opts)
-            infos.append(info)
-        return infos
+        if args.solver == "single":
+            infos = []
+            for _, d, e in dev_mats:
+                _, _, info = mr3.stemr(d, e, opts=opts)
+                infos.append(info)
+            return infos
+        _, _, _, _, info = mr3.stemr_batched(n_off, dcat, ecat, opts=opts)
+        return [info]
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -268,21 +280,21 @@ def run_gpu(args, cfg, rank, world):
                 "peak_source": "FP64 pipe: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz",
                 "kernel_share": float(ms / max(g.sum(), 1e-9))}
 
-    # ---- end to end through the host-buffer entry point (pinned host memory)
-    e2e = None
-    if rank == 0 or True:
-        hbuf = []
-        nmax = max(len(d) for _, d, _ in mats)
+    # ---- end to end through the public API: every step copies its inputs from pinned host
+    # memory to the device, solves, and reads w and Z back into pinned host memory
+    import ctypes
+    L = mr3.lib()
+    nmax = max(sizes)
+    if args.solver == "single":
         Zh = torch.empty((nmax, nmax), dtype=torch.float64, pin_memory=True).numpy()
         wh = torch.empty(nmax, dtype=torch.float64, pin_memory=True).numpy()
+        hbuf = []
         for _, d, e in mats:
             dh = torch.empty(len(d), dtype=torch.float64, pin_memory=True).numpy()
             eh = torch.empty(max(len(e), 1), dtype=torch.float64, pin_memory=True).numpy()
             dh[:] = d
             eh[: len(e)] = e
             hbuf.append((dh, eh))
-        import ctypes
-        L = mr3.lib()
 
         def e2e_step():
             for dh, eh in hbuf:
@@ -294,18 +306,33 @@ def run_gpu(args, cfg, rank, world):
                                       Zh.ctypes.data_as(ctypes.c_void_p), n, None, None,
                                       ctypes.c_void_p(stream.cuda_stream))
                 assert rc in (0, 1, 2), rc
+    else:
+        dh = torch.tensor(dcat_h).pin_memory()
+        eh = torch.tensor(ecat_h).pin_memory()
+        zlen = int(sum(n * n for n in sizes))
+        wh = torch.empty(int(n_off[-1]), dtype=torch.float64, pin_memory=True)
+        Zh = torch.empty(zlen, dtype=torch.float64, pin_memory=True)
+        dd_, ed_ = torch.empty_like(dcat), torch.empty_like(ecat)
+
+        def e2e_step():
+            dd_.copy_(dh, non_blocking=True)
+            ed_.copy_(eh, non_blocking=True)
+            _, w, Z, _, _ = mr3.stemr_batched(n_off, dd_, ed_)
+            wh.copy_(w[: wh.numel()], non_blocking=True)
+            Zh.copy_(Z[:zlen], non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+    e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ne = max(2, min(args.steps, 5))
+    for _ in range(ne):
         e2e_step()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ne = max(2, min(args.steps, 5))
-        for _ in range(ne):
-            e2e_step()
-        torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - t0) / ne
-        h2d = sum(8 * (len(d) + len(e)) for _, d, e in mats)
-        d2h = sum(8 * (len(d) + len(d) * len(d)) for _, d, _ in mats)
-        e2e = {"value": world * units_per_step / e2e_s, "unit": "eigenpairs/s",
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / ne
+    h2d = sum(8 * (len(d) + len(e)) for _, d, e in mats)
+    d2h = sum(8 * (len(d) + len(d) * len(d)) for _, d, _ in mats)
+    e2e = {"value": world * units_per_step / e2e_s, "unit": "eigenpairs/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -319,16 +346,19 @@ def run_gpu(args, cfg, rank, world):
                        "n": [len(d) for _, d, _ in mats],
                        "matrices_per_step": len(mats), "l2": "flushed between steps "
                        "(256 MiB device write outside the per-step events)",
-                       "parallelism": "replicas, one set of matrices per GPU"},
+                       "parallelism": "replicas, one set of matrices per GPU",
+                       "solver": args.solver},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(agg["kernel_launches"].sum()),
             "clocks": clk, "wall_s": wall,
-            "per_matrix": [dict(kind=k, **{key: inf[key] for key in (
+            "solver": "mr3_stemr_batched over the step's matrices" if args.solver == "batched"
+                      else "one mr3_stemr call per matrix",
+            "solve_info": [dict(**{key: inf[key] for key in (
                 "dmax", "largest_cluster", "nclusters", "new_rrr", "untested_rrr", "rqi_iters",
                 "rqi_iters_max", "bisect_fallbacks", "sturm_steps", "shift_steps",
                 "twisted_steps", "status")},
                 kernel_ms=[round(x, 3) for x in inf["kernel_ms"]])
-                for (k, _, _), inf in zip(mats, last_infos or [])],
+                for inf in (last_infos or [])],
             "step_ms": [round(x, 3) for x in step_ms]}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -475,6 +505,9 @@ def main():
     ap.add_argument("--backward", action="store_true",
                     help="time the backward pass against the forward instead")
     ap.add_argument("--n-bwd", type=int, default=4096)
+    ap.add_argument("--solver", default="batched", choices=["batched", "single"],
+                    help="the step's matrices in one mr3_stemr_batched call, or one mr3_stemr "
+                         "call each")
     ap.add_argument("--subset", action="store_true",
                     help="time the n=20000 glued Wilkinson subset, binary64 vs double-double")
     args = ap.parse_args()

@@ -141,9 +141,9 @@ __global__ void __launch_bounds__(32) k_rqi(int nsingle, const SingleItem *__res
         const bool active = idx < nsingle;
         // ---- singleton data (every lane of the team holds a copy)
         int c = 0, n = 1, j = 1;
-        const double *d = pool, *dl = pool, *dll = pool, *Qm = pool, *iQm = pool;
+        const double *d = pool, *dll = pool, *Qm = pool, *iQm = pool;
         const int *Qe = (const int *)pool;
-        double l = 0.0, h = 0.0, gap = 1.0, sigma = 0.0;
+        double l = 0.0, h = 0.0, gap = 1.0;
         double *zc = Z;
         const double *td = Din, *te = Ein;
         if (active) {
@@ -154,7 +154,6 @@ __global__ void __launch_bounds__(32) k_rqi(int nsingle, const SingleItem *__res
             const MatDesc M = mats[B.mat];
             n = B.n;
             d = pool + N.rep;
-            dl = d + n;
             dll = d + 2 * n;
             Qm = d + rep_q_offset(n);
             iQm = Qm + n;
@@ -164,7 +163,6 @@ __global__ void __launch_bounds__(32) k_rqi(int nsingle, const SingleItem *__res
             h = hi[c];
             gap = fmin(gapl[c], gapr[c]);
             if (!(gap > 0.0)) gap = kSafmin;
-            sigma = N.sigma;
             zc = Z + M.zoff + (long long)(c - M.woff) * M.ldz + B.roff;
             td = Din + B.off;
             te = Ein + B.off;
@@ -375,7 +373,6 @@ __global__ void __launch_bounds__(32) k_rqi(int nsingle, const SingleItem *__res
             nfb += fb ? 1 : 0;
             ncap += capped ? 1 : 0;
         }
-        (void)sigma;
         __syncwarp();
     }
     for (int o = 16; o > 0; o >>= 1) {

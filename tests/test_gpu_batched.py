@@ -106,3 +106,16 @@ def test_batched_workload_sample(cuda):
                                                              e[n_off[b]:n_off[b + 1] - 1]))
     for (db, eb), (w, Z) in zip(mats, out):
         check_eigenpairs(db, eb, w, Z, vec_compare=False)
+
+
+def test_batched_bench_step(cuda):
+    # the n = 8192 step (1-2-1, Wilkinson W+, uniform(-1,1) seeds 201, 202) in one batched
+    # call, as the benchmark times it: every matrix within the parity gates (the Wilkinson
+    # matrix with the tight-pair gate of the binary64 tree)
+    from _checks import check_eigenpairs
+    mats = [tm.make("one_two_one", 8192), tm.make("wilkinson", 8192),
+            tm.random_uniform(8192, 201, 202)]
+    gates = [10.0, 1000.0, 10.0]
+    mats_out, out, info = _batched([8192, 8192, 8192], fill=lambda b, n: mats[b])
+    for (d, e), (wb, Zb), gate in zip(mats, out, gates):
+        check_eigenpairs(d, e, wb, Zb, orth_gate=gate, vec_compare=False)
