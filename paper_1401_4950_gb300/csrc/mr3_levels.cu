@@ -503,15 +503,22 @@ __device__ void trial_shift(int n, const double *__restrict__ d, const double *_
     double a = -tau, cp = 1.0;
     bool ok = is_finite(tau);
     double g = 0.0;
+    // operands of step i + 1 are loaded while step i runs (software prefetch)
+    double dn = __ldg(d), ln = (n > 1) ? __ldg(dll) : 0.0;
     for (int i = 0; i < n; ++i) {
-        double c = fma(__ldg(d + i), cp, a);
+        const double di = dn, li = ln;
+        if (i + 1 < n) {
+            dn = __ldg(d + i + 1);
+            ln = (i + 1 < n - 1) ? __ldg(dll + i + 1) : 0.0;
+        }
+        double c = fma(di, cp, a);
         if (is_zero(c)) { ok = false; c = -cp * 0x1p-80; }
         // running max of |c_i / c_{i-1}|, dividing only when it may grow
         if (fabs(c) > g * fabs(cp)) g = fmax(g, fabs(c / cp));
         if (!is_finite(c)) ok = false;
         int k = 0;
         if (i < n - 1) {
-            const double t = __ldg(dll + i) * a;
+            const double t = li * a;
             a = fma(-tau, c, t);
             const int ex = biased_exp(c);
             if ((unsigned)(ex - (1023 - 200)) > 400u) {

@@ -431,10 +431,16 @@ __device__ void factor_root(int n, const double *__restrict__ d, const double *_
     double pm2 = 0.0, pm1 = 1.0;
     bool ok = true;
     double g = 0.0;
+    // operands of step i + 1 are loaded while step i runs (software prefetch)
+    double dn = __ldg(d), bn = 0.0;
     for (int i = 0; i < n; ++i) {
-        const double ai = __ldg(d + i) - mu;
+        const double ai = dn - mu, b = bn;
+        if (i + 1 < n) {
+            dn = __ldg(d + i + 1);
+            bn = __ldg(e + i);
+        }
         double q = 0.0;
-        if (i > 0) { const double b = __ldg(e + i - 1); q = (b * b) * pm2; }
+        if (i > 0) q = (b * b) * pm2;
         double p = fma(ai, pm1, -q);
         P[i] = p;
         const int neg = sign_bit(p) ^ sign_bit(pm1);
