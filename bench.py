@@ -210,7 +210,7 @@ def run_gpu(args, cfg, rank, world):
     dev_mats = [(k, torch.tensor(d, device=dev), torch.tensor(e, device=dev)) for k, d, e in mats]
     units_per_step = sum(len(d) for _, d, _ in mats)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    opts = mr3.make_opts(profile=1)
+    opts = mr3.make_opts(profile=1, prec=mr3.DD if args.prec == "dd" else mr3.FP64)
     stream = torch.cuda.current_stream()
     # the step's matrices packed for one mr3_stemr_batched call (d and e with the same
     # offsets, the last e slot of each matrix unused)
@@ -266,18 +266,27 @@ def run_gpu(args, cfg, rank, world):
     ms_per_step = tot_ms / args.steps
     value = job_value(units_per_step, world, ms_per_step)
 
-    # ---- dominant kernel and its roofline (FP64 pipe)
+    # ---- dominant kernel group and its roofline (FP64 pipe).  Algorithmic work per unit
+    # (App. B recurrences): a Sturm-count step 5 flops (add, divide, multiply, FMA), a
+    # dstqds trial step 5, a twisted-factorization step 5.5; the units are the steps the
+    # library counts on the device, the time the group's CUDA events on its stream.
     g = agg["kernel_ms"]
-    groups = {"k_bisect": (g[2] + g[6], agg["kernel_launches"][2] + agg["kernel_launches"][6],
-                           5.0 * agg["sturm_steps"]),
-              "k_rqi": (g[4], agg["kernel_launches"][4], 5.5 * agg["twisted_steps"]),
-              "k_shift": (g[5], agg["kernel_launches"][5], 5.0 * agg["shift_steps"])}
+    kl = agg["kernel_launches"]
+    groups = {"k_bisect2 (root and child refinement)":
+                  (g[2] + g[6], kl[2] + kl[6], agg["sturm_steps"], "Sturm step", 5.0),
+              "k_rqi": (g[4], kl[4], agg["twisted_steps"], "twisted-factorization step", 5.5),
+              "k_refine_ends + k_shift_*": (g[5], kl[5], agg["shift_steps"],
+                                            "cluster-end Sturm / dstqds step", 5.0)}
     dom = max(groups, key=lambda k: groups[k][0])
-    ms, launches, flops = groups[dom]
-    achieved = (flops / max(launches, 1)) / (ms / max(launches, 1) / 1e3) / 1e12 if ms > 0 else 0.0
+    ms, launches, units, unit_name, fpu = groups[dom]
+    achieved = (fpu * units / 1e12) / (ms / 1e3) if ms > 0 else 0.0
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "FP64 pipe: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                "peak_source": "FP64 pipe: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (no FP64 "
+                               "figure in the measured peaks)",
+                "algorithmic": {"unit": unit_name, "flops_per_unit": fpu,
+                                "units_per_launch": units / max(launches, 1),
+                                "ms_per_launch": ms / max(launches, 1)},
                 "kernel_share": float(ms / max(g.sum(), 1e-9))}
 
     # ---- end to end through the public API: every step copies its inputs from pinned host
@@ -303,8 +312,8 @@ def run_gpu(args, cfg, rank, world):
                 rc = L.mr3_stemr_host(n, dh.ctypes.data_as(ctypes.c_void_p),
                                       eh.ctypes.data_as(ctypes.c_void_p), 0, 0.0, 0.0, 1, n,
                                       ctypes.byref(m), wh.ctypes.data_as(ctypes.c_void_p),
-                                      Zh.ctypes.data_as(ctypes.c_void_p), n, None, None,
-                                      ctypes.c_void_p(stream.cuda_stream))
+                                      Zh.ctypes.data_as(ctypes.c_void_p), n, ctypes.byref(opts),
+                                      None, ctypes.c_void_p(stream.cuda_stream))
                 assert rc in (0, 1, 2), rc
     else:
         dh = torch.tensor(dcat_h).pin_memory()
@@ -317,7 +326,7 @@ def run_gpu(args, cfg, rank, world):
         def e2e_step():
             dd_.copy_(dh, non_blocking=True)
             ed_.copy_(eh, non_blocking=True)
-            _, w, Z, _, _ = mr3.stemr_batched(n_off, dd_, ed_)
+            _, w, Z, _, _ = mr3.stemr_batched(n_off, dd_, ed_, opts=opts)
             wh.copy_(w[: wh.numel()], non_blocking=True)
             Zh.copy_(Z[:zlen], non_blocking=True)
             torch.cuda.current_stream().synchronize()
@@ -347,7 +356,8 @@ def run_gpu(args, cfg, rank, world):
                        "matrices_per_step": len(mats), "l2": "flushed between steps "
                        "(256 MiB device write outside the per-step events)",
                        "parallelism": "replicas, one set of matrices per GPU",
-                       "solver": args.solver},
+                       "solver": args.solver,
+                       "tree": "double-double (Ch. 5)" if args.prec == "dd" else "binary64"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(agg["kernel_launches"].sum()),
             "clocks": clk, "wall_s": wall,
@@ -508,6 +518,8 @@ def main():
     ap.add_argument("--solver", default="batched", choices=["batched", "single"],
                     help="the step's matrices in one mr3_stemr_batched call, or one mr3_stemr "
                          "call each")
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "dd"],
+                    help="representation tree in binary64 or double-double (Ch. 5)")
     ap.add_argument("--subset", action="store_true",
                     help="time the n=20000 glued Wilkinson subset, binary64 vs double-double")
     args = ap.parse_args()

@@ -288,7 +288,7 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
     const long long scratch_cap_bytes = 2ll << 30; // RQI scratch budget per launch
     int status = 0;
     auto run_singles = [&](int level, const LevelCounters &hc) -> int {
-        const int team = dd ? 0 : rqi_team(hc.nsingle);
+        const int team = dd ? 0 : rqi_team(hc.nsingle, nmat);
         long long slots = dd ? rqi_dd_threads(hc.nsingle, nmax, 2 * scratch_cap_bytes)
                              : rqi_slots(hc.nsingle, nmax, scratch_cap_bytes, team);
         const size_t per_slot = dd ? (size_t)4 * nmax : (size_t)rqi_scratch_per_index(team) * nmax;

@@ -81,9 +81,10 @@ void launch_rqi(int nsingle, const SingleItem *singles, const Node *nodes, const
                 int max_rqi, unsigned fault_mask, int *work_counter, DevInfo *info,
                 int team, cudaStream_t s);
 
-// Team size (lanes per singleton, 2 or 8) for a launch of nsingle singletons; scratch doubles
+// Team size (lanes per singleton, 2 or 8) for a launch of nsingle singletons of a solve over
+// nmat matrices; scratch doubles
 // per index per warp slot, and singletons a warp slot holds at a time, for that team size.
-int rqi_team(long long nsingle);
+int rqi_team(long long nsingle, int nmat);
 int rqi_scratch_per_index(int team);
 int rqi_singles_per_slot(int team);
 

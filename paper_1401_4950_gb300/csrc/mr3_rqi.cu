@@ -413,8 +413,19 @@ void launch_rqi(int nsingle, const SingleItem *singles, const Node *nodes, const
 }
 
 // Teams of 2 once the singletons clearly outnumber what the resident warps hold with teams
-// of 8 (about 17 warps per SM at this kernel's register count, 4 singletons each).
-int rqi_team(long long nsingle) { return nsingle > 32768 ? 2 : 8; }
+// of 8 (about 17 warps per SM at this kernel's register count, 4 singletons each).  When a
+// solve covers several matrices the singleton launch runs beside the other matrices' shift
+// and refinement kernels on the main stream, and its fewer binary64 instructions with teams
+// of 2 pay off from much smaller counts (measured on the n = 8192 three-matrix step).
+#ifndef MR3_RQI_TEAM2_MIN
+#define MR3_RQI_TEAM2_MIN 32768
+#endif
+#ifndef MR3_RQI_TEAM2_MIN_MULTI
+#define MR3_RQI_TEAM2_MIN_MULTI 2048
+#endif
+int rqi_team(long long nsingle, int nmat) {
+    return nsingle > (nmat > 1 ? MR3_RQI_TEAM2_MIN_MULTI : MR3_RQI_TEAM2_MIN) ? 2 : 8;
+}
 int rqi_scratch_per_index(int team) { return kScratchPerSingleton * (32 / team); }
 int rqi_singles_per_slot(int team) { return 32 / team; }
 
