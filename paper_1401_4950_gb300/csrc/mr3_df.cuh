@@ -56,6 +56,39 @@ __device__ __forceinline__ dfloat df_mul(dfloat x, dfloat y) {
 
 __device__ __forceinline__ dfloat df_neg(dfloat x) { return {-x.h, -x.l}; }
 
+// x y + z in one pass: the leading product exactly (TwoProd by FMA), the cross terms and
+// the low words in single rounding, one TwoSum of the leading parts and a final Fast2Sum.
+// The error is a few units of 2^-48 times |x y| + |z| (not of the result): in the Sturm
+// count that is a relative perturbation of d_i and of s_i, which the mixed stability of
+// dstqds admits, so the count stays exact for a slightly perturbed representation.
+__device__ __forceinline__ dfloat df_fma(dfloat x, dfloat y, dfloat z) {
+    const float p = __fmul_rn(x.h, y.h);
+    const float pe = __fmaf_rn(x.h, y.h, -p);
+    const float t = __fmaf_rn(x.h, y.l, __fmul_rn(x.l, y.h));
+    float s, e;
+    two_sum(p, z.h, s, e);
+    const float lo = __fadd_rn(e, __fadd_rn(pe, __fadd_rn(t, z.l)));
+    dfloat r;
+    fast_two_sum(s, lo, r.h, r.l);
+    return r;
+}
+
+// x1 y1 + x2 y2 in one pass (same construction and error form as df_fma).
+__device__ __forceinline__ dfloat df_dot2(dfloat x1, dfloat y1, dfloat x2, dfloat y2) {
+    const float p1 = __fmul_rn(x1.h, y1.h);
+    const float e1 = __fmaf_rn(x1.h, y1.h, -p1);
+    const float t1 = __fmaf_rn(x1.h, y1.l, __fmul_rn(x1.l, y1.h));
+    const float p2 = __fmul_rn(x2.h, y2.h);
+    const float e2 = __fmaf_rn(x2.h, y2.h, -p2);
+    const float t2 = __fmaf_rn(x2.h, y2.l, __fmul_rn(x2.l, y2.h));
+    float s, e;
+    two_sum(p1, p2, s, e);
+    const float lo = __fadd_rn(e, __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(t1, t2)));
+    dfloat r;
+    fast_two_sum(s, lo, r.h, r.l);
+    return r;
+}
+
 // Nearest double-float to a double (exact when the double has at most 48 significant
 // bits); the tail is computed in binary64 once per datum.
 __device__ __forceinline__ dfloat df_from(double x) {
@@ -86,13 +119,13 @@ __device__ __forceinline__ int negcount_df(int n, const float4 *__restrict__ dd,
         const float4 q = qn;
         if (i + 1 < n) qn = __ldg(dd + i + 1);
         const dfloat di = {q.x, q.y};
-        dfloat c = df_add(df_mul(di, cp), a);
+        dfloat c = df_fma(di, cp, a);
         if (c.h == 0.f) { c.h = -cp.h * 0x1p-30f; c.l = 0.f; }
         const int sc = __float_as_int(c.h) < 0 ? 1 : 0;
         cnt += sc ^ sp;
         if (i < n - 1) {
             const dfloat dlli = {q.z, q.w};
-            a = df_add(df_mul(dlli, a), df_mul(ns, c));
+            a = df_dot2(dlli, a, ns, c);
             const int ex = (__float_as_int(c.h) >> 23) & 0xff;
             if ((unsigned)(ex - (127 - 40)) > 80u) {
                 if (ex == 0xff) return -1;

@@ -433,6 +433,36 @@ __global__ void k_refine_ends(int ncluster, const ClusterItem *__restrict__ clus
         if (phase == 1) nb = carry[g].x;
     }
     unsigned long long steps = 0;
+    if (phase == 1) {
+        // the double-float phase's bounds hold for its perturbed copy of the representation:
+        // verify them with binary64 counts and widen by that copy's error bound if needed
+        const double kap = 32.0 * n * 0x1p-47;
+        for (int attempt = 0; attempt < 6; ++attempt) {
+            int okL = 1, okH = 1;
+            if (active) {
+                if (E >= 2) {
+                    int cnt = 0;
+                    if (k < 2) { cnt = negcount_ldl(n, pd, pd + 2 * n, k == 0 ? L : H); steps += n; }
+                    okL = __shfl_sync(gmask, cnt, gbase) < tgt;
+                    okH = __shfl_sync(gmask, cnt, gbase + 1) >= tgt;
+                } else {
+                    okL = negcount_ldl(n, pd, pd + 2 * n, L) < tgt;
+                    okH = negcount_ldl(n, pd, pd + 2 * n, H) >= tgt;
+                    steps += 2ull * n;
+                }
+            } else if (E >= 2) {
+                (void)__shfl_sync(gmask, 0, gbase);
+                (void)__shfl_sync(gmask, 0, gbase + 1);
+            }
+            const bool ok = okL && okH;
+            if (__all_sync(0xffffffffu, ok || !active)) break;
+            if (active && !ok) {
+                const double f = ldexp(kap, 4 * attempt);
+                if (!okL) L -= f * fmax(fabs(L), kSafmin);
+                if (!okH) H += f * fmax(fabs(H), kSafmin);
+            }
+        }
+    }
     for (int sweep = 0; sweep < 64; ++sweep) {
         const double w = H - L;
         const double gap_lb = side ? (L - nb) : (nb - H);
