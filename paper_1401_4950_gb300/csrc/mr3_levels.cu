@@ -531,8 +531,11 @@ __device__ void trial_shift(int n, const double *__restrict__ d, const double *_
                             double tau, bool store, double *U, int *K, int kstride, bool &exists,
                             double &growth) {
     double a = -tau, cp = 1.0;
-    bool ok = is_finite(tau);
-    double g = 0.0;
+    bool zero = false;
+    // running maximum of |c_i / c_{i-1}| kept as a fraction gn / gd: no division and no
+    // data-dependent branch on the recurrence's critical path (non-finite values propagate
+    // and are caught once at the end)
+    double gn = 0.0, gd = 1.0;
     // operands of step i + 1 are loaded while step i runs (software prefetch)
     double dn = __ldg(d), ln = (n > 1) ? __ldg(dll) : 0.0;
     for (int i = 0; i < n; ++i) {
@@ -542,23 +545,23 @@ __device__ void trial_shift(int n, const double *__restrict__ d, const double *_
             ln = (i + 1 < n - 1) ? __ldg(dll + i + 1) : 0.0;
         }
         double c = fma(di, cp, a);
-        if (is_zero(c)) { ok = false; c = -cp * 0x1p-80; }
-        // running max of |c_i / c_{i-1}|, dividing only when it may grow
-        if (fabs(c) > g * fabs(cp)) g = fmax(g, fabs(c / cp));
-        if (!is_finite(c)) ok = false;
+        const bool z = is_zero(c);
+        zero |= z;
+        c = z ? -cp * 0x1p-80 : c;
+        const double ac = fabs(c), acp = fabs(cp);
+        const bool up = ac * gd > gn * acp;
+        gn = up ? ac : gn;
+        gd = up ? acp : gd;
         int k = 0;
         if (i < n - 1) {
-            const double t = li * a;
-            a = fma(-tau, c, t);
+            a = fma(-tau, c, li * a);
+            if (store) U[i] = c;
             const int ex = biased_exp(c);
             if ((unsigned)(ex - (1023 - 200)) > 400u) {
                 k = 1023 - ex;
-                const double s = pow2i(k);
-                if (store) U[i] = c;
-                c *= s;
-                a *= s;
-            } else if (store) {
-                U[i] = c;
+                const double sc = pow2i(k);
+                c *= sc;
+                a *= sc;
             }
         } else if (store) {
             U[i] = c;
@@ -566,7 +569,8 @@ __device__ void trial_shift(int n, const double *__restrict__ d, const double *_
         if (store) K[(size_t)i * kstride] = k;
         cp = c;
     }
-    exists = ok && is_finite(g);
+    const double g = gn / gd;
+    exists = is_finite(tau) && !zero && is_finite(g) && is_finite(cp) && is_finite(a);
     growth = exists ? g : INFINITY;
 }
 
