@@ -59,8 +59,6 @@ __global__ void k_root_dd(int nblk, BlkDesc *blks, const double *__restrict__ D,
     double *h0 = pool0 + B.rep, *l0 = pool0_lo + B.rep;
     const double mu = B.mu, xi = 8.0 * kEps;
     ddouble pm2 = dd_make(0.0), pm1 = dd_make(1.0);
-    float4 *rdf = (float4 *)(h0 + rep_df_offset(n));
-    bool dfok = true;
     for (int i = 0; i < n; ++i) {
         ddouble a;
         dd_two_sum(__ldg(d + i), -mu, a.h, a.l);
@@ -82,19 +80,26 @@ __global__ void k_root_dd(int nblk, BlkDesc *blks, const double *__restrict__ D,
         h0[i] = dp.h;          l0[i] = dp.l;
         h0[n + i] = dl.h;      l0[n + i] = dl.l;
         h0[2 * n + i] = dll.h; l0[2 * n + i] = dll.l;
-        const dfloat fa = df_from(dp.h), fc = df_from(dll.h);
-        rdf[i] = make_float4(fa.h, fa.l, fc.h, fc.l);
-        dfok &= df_safe(dp.h) && df_safe(dll.h) && is_finite(dp.h) && is_finite(dll.h);
         const double s = rescale_factor(p.h);
         if (s != 1.0) { p = dd_scale(p, s); pm1 = dd_scale(pm1, s); }
         pm2 = pm1;
         pm1 = p;
     }
     // the bisection's double-float copy is rewritten from these leading words
+    int dfexp;
+    const bool dfok = df_write_copy_serial(n, h0, h0 + 2 * n, (float4 *)(h0 + rep_df_offset(n)), dfexp);
     blks[b].dfok = dfok ? 1 : 0;
+    blks[b].dfexp = dfexp;
 }
 
 // ---------------------------------------------------------------- child representations
+
+// Substitute for an exactly zero pivot d_i + s_i of the divided recurrences below: a
+// number 2^-120 times |d_i| (below the double-double roundoff, so the count is that of
+// the limit), at least 2^-1000 so that it stays normal.
+__device__ __forceinline__ double dd_tiny_pivot(double di) {
+    return fmax(fabs(di) * 0x1p-120, 0x1p-1000);
+}
 
 // One thread per cluster: L+ D+ L+^T = L D L^T - tau I in double-double by the homogeneous
 // dstqds recurrence c_i = d_i c_{i-1} + a_i, a_{i+1} = dll_i a_i - tau c_i (c_i is the
@@ -114,16 +119,13 @@ __global__ void k_shift_dd(int ncluster, const ClusterItem *__restrict__ cluster
     const double *ph = pool + P.rep, *pl = pool_lo + P.rep;
     double *ch = childpool + cluster_rep[ci], *cl = childpool_lo + cluster_rep[ci];
     const double tau = child_tau[ci];
-    float4 *cdf = (float4 *)(ch + rep_df_offset(n));
-    bool dfok = true;
     ddouble a = dd_make(-tau), cp = dd_make(1.0);
     for (int i = 0; i < n; ++i) {
         ddouble c = dd_add(dd_mul(dd_load(ph, pl, i), cp), a);
-        if (is_zero(c.h)) c = dd_make(-cp.h * 0x1p-80);
+        if (is_zero(c.h)) c = dd_make(-cp.h * dd_tiny_pivot(ph[i]));
         const ddouble dp = dd_div(c, cp);
         ch[i] = dp.h;
         cl[i] = dp.l;
-        double dllh = 0.0;
         if (i < n - 1) {
             const ddouble dl = dd_load(ph, pl, n + i);
             const ddouble dllp = dd_div(dd_mul(dl, dl), dp);
@@ -131,7 +133,6 @@ __global__ void k_shift_dd(int ncluster, const ClusterItem *__restrict__ cluster
             cl[n + i] = dl.l;
             ch[2 * n + i] = dllp.h;
             cl[2 * n + i] = dllp.l;
-            dllh = dllp.h;
             a = dd_sub(dd_mul(dd_load(ph, pl, 2 * n + i), a), dd_mul_d(c, tau));
             const double s = rescale_factor(c.h);
             if (s != 1.0) { c = dd_scale(c, s); a = dd_scale(a, s); }
@@ -139,13 +140,13 @@ __global__ void k_shift_dd(int ncluster, const ClusterItem *__restrict__ cluster
             ch[n + i] = 0.0;     cl[n + i] = 0.0;
             ch[2 * n + i] = 0.0; cl[2 * n + i] = 0.0;
         }
-        // the bisection's double-float copy, rewritten from this child's leading words
-        const dfloat fa = df_from(dp.h), fc = df_from(dllh);
-        cdf[i] = make_float4(fa.h, fa.l, fc.h, fc.l);
-        dfok &= df_safe(dp.h) && df_safe(dllh) && is_finite(dp.h) && is_finite(dllh);
         cp = c;
     }
+    // the bisection's double-float copy, rewritten from this child's leading words
+    int dfexp;
+    const bool dfok = df_write_copy_serial(n, ch, ch + 2 * n, (float4 *)(ch + rep_df_offset(n)), dfexp);
     child_nodes[ci].dfok = dfok ? 1 : 0;
+    child_nodes[ci].dfexp = dfexp;
     atomicAdd(&info->shift_steps, (unsigned long long)n);
 }
 
@@ -158,7 +159,7 @@ __device__ int negcount_dd(int n, const double *__restrict__ h, const double *__
     int cnt = 0;
     for (int i = 0; i < n; ++i) {
         ddouble dp = dd_add(dd_load(h, l, i), s);
-        if (is_zero(dp.h)) dp = dd_make(-0x1p-1000);
+        if (is_zero(dp.h)) dp = dd_make(-dd_tiny_pivot(h[i]));
         cnt += dd_neg_sign(dp) ? 1 : 0;
         if (i < n - 1) s = dd_sub(dd_mul(dd_load(h, l, 2 * n + i), dd_div(s, dp)), sigma);
     }
@@ -222,7 +223,7 @@ __global__ void __launch_bounds__(128) k_rqi_dd(
             int negc = 0;
             for (int i = 0; i < n - 1; ++i) {
                 ddouble dp = dd_add(dd_load(Rh, Rl, i), s);
-                if (is_zero(dp.h)) dp = dd_make(-0x1p-1000);
+                if (is_zero(dp.h)) dp = dd_make(-dd_tiny_pivot(Rh[i]));
                 negc += dd_neg_sign(dp) ? 1 : 0;
                 const ddouble rdp = dd_rcp(dp);
                 const ddouble lp = dd_mul(dd_load(Rh, Rl, n + i), rdp);
@@ -234,7 +235,7 @@ __global__ void __launch_bounds__(128) k_rqi_dd(
             }
             {
                 ddouble dp = dd_add(dd_load(Rh, Rl, n - 1), s);
-                if (is_zero(dp.h)) dp = dd_make(-0x1p-1000);
+                if (is_zero(dp.h)) dp = dd_make(-dd_tiny_pivot(Rh[n - 1]));
                 negc += dd_neg_sign(dp) ? 1 : 0;
             }
             // ---- backward, gamma and the twist index
@@ -244,7 +245,7 @@ __global__ void __launch_bounds__(128) k_rqi_dd(
             double agmin = fabs(gam.h);
             for (int i = n - 2; i >= 0; --i) {
                 ddouble rr = dd_add(dd_load(Rh, Rl, 2 * n + i), p);
-                if (is_zero(rr.h)) rr = dd_make(0x1p-1000);
+                if (is_zero(rr.h)) rr = dd_make(dd_tiny_pivot(Rh[2 * n + i]));
                 const ddouble rrr = dd_rcp(rr);
                 const ddouble um = dd_mul(dd_load(Rh, Rl, n + i), rrr);
                 const ddouble x = dd_mul(dd_mul(p, dd_load(Rh, Rl, i)), rrr); // p_i + lam

@@ -48,7 +48,8 @@ struct BlkDesc {
     int roff;       // first row inside the matrix
     int j0, j1;     // local eigenvalue indices selected (1-based, inclusive; j1 < j0: none)
     int col0;       // global column of local index j0
-    int dfok;       // the root's double-float copy keeps full precision
+    int dfok;       // the root's double-float copy is usable (see df_entry_ok)
+    int dfexp;      // the copy holds 2^dfexp (d, dll)
     double gl, gu;  // Gershgorin interval of the block
     double mu;      // root shift: M_root = T_block - mu I (before the random perturbation)
     double spdiam;  // gu - gl
@@ -61,7 +62,8 @@ struct Node {
     int blk;           // owning block
     int c0, c1;        // global columns (inclusive)
     int depth;
-    int dfok;          // the double-float copy keeps full precision (see df_safe)
+    int dfok;          // the double-float copy is usable (see df_entry_ok)
+    int dfexp;         // the copy holds 2^dfexp (d, dll)
     double sigma;      // eigenvalue of T = eigenvalue of the representation + sigma
     double lnb, rnb;   // bounds (in this representation's coordinates) of the nearest
                        // eigenvalues outside [c0, c1]: upper bound of the left one, lower
@@ -146,9 +148,13 @@ __device__ __forceinline__ double splitmix_pm1(unsigned long long seed, unsigned
 // d_i or dll_i as an O(eps) relative perturbation (the pair (a, c) only shares a
 // positive scale), so the count is exact for a relatively perturbed representation,
 // the property bisection on an RRR relies on.  (a, c) are rescaled by a power of two
-// when c leaves [2^-200, 2^200].  A pivot that is exactly zero is replaced by a tiny
-// negative one (SignBit(-0) = 1, App. B remarks).  Critical path: two dependent FMAs
-// per step.
+// when c leaves [2^-200, 2^200].  A pivot that is exactly zero counts as negative, the
+// limit sigma -> sigma+ (SignBit(-0) = 1, App. B remarks), and c_i = 0 is kept: the
+// homogeneous form needs no division, the next step gives c_{i+1} = dll_i a_i, and its
+// pivot d+_{i+1} = c_{i+1} / c_i is the limit +infinity, counted positive because
+// sign(c_{i+1}) = sign(c_{i-1}) xor 1 when dll_i and d_i share a sign.  A tiny substitute
+// pivot would have to be tiny relative to the data, which carry no fixed scale.  Critical
+// path: two dependent FMAs per step.
 __device__ __forceinline__ int negcount_ldl(int n, const double *__restrict__ d,
                                             const double *__restrict__ dll, double sigma) {
     double a = -sigma, cp = 1.0;
@@ -160,12 +166,12 @@ __device__ __forceinline__ int negcount_ldl(int n, const double *__restrict__ d,
         ln = (i + 1 < n - 1) ? __ldg(dll + i + 1) : 0.0;
         const double t = li * a;
         double c = fma(di, cp, a);
-        if (is_zero(c)) c = -cp * 0x1p-80;
-        const int sc = sign_bit(c);
+        const bool z = is_zero(c);
+        const int sc = z ? (sp ^ 1) : sign_bit(c);
         cnt += sc ^ sp;
         a = fma(-sigma, c, t);
         const int ex = biased_exp(c);
-        if ((unsigned)(ex - (1023 - 200)) > 400u) {
+        if ((unsigned)(ex - (1023 - 200)) > 400u && !z) {
             const double s = pow2i(1023 - ex);
             c *= s;
             a *= s;
@@ -190,16 +196,15 @@ __device__ __forceinline__ void negcount_ldl2(int n, const double *__restrict__ 
         const double di = __ldg(d + i), li = __ldg(dll + i);
         const double t0 = li * a0, t1 = li * a1;
         double x0 = fma(di, c0, a0), x1 = fma(di, c1, a1);
-        if (is_zero(x0)) x0 = -c0 * 0x1p-80;
-        if (is_zero(x1)) x1 = -c1 * 0x1p-80;
-        const int q0 = sign_bit(x0), q1 = sign_bit(x1);
+        const bool z0 = is_zero(x0), z1 = is_zero(x1);
+        const int q0 = z0 ? (p0 ^ 1) : sign_bit(x0), q1 = z1 ? (p1 ^ 1) : sign_bit(x1);
         n0 += q0 ^ p0;
         n1 += q1 ^ p1;
         a0 = fma(-s0, x0, t0);
         a1 = fma(-s1, x1, t1);
         const int e0 = biased_exp(x0), e1 = biased_exp(x1);
-        if ((unsigned)(e0 - (1023 - 200)) > 400u) { const double s = pow2i(1023 - e0); x0 *= s; a0 *= s; }
-        if ((unsigned)(e1 - (1023 - 200)) > 400u) { const double s = pow2i(1023 - e1); x1 *= s; a1 *= s; }
+        if ((unsigned)(e0 - (1023 - 200)) > 400u && !z0) { const double s = pow2i(1023 - e0); x0 *= s; a0 *= s; }
+        if ((unsigned)(e1 - (1023 - 200)) > 400u && !z1) { const double s = pow2i(1023 - e1); x1 *= s; a1 *= s; }
         c0 = x0; c1 = x1; p0 = q0; p1 = q1;
     }
     double x0 = fma(__ldg(d + n - 1), c0, a0), x1 = fma(__ldg(d + n - 1), c1, a1);
@@ -221,11 +226,11 @@ __device__ __forceinline__ int negcount_T_f32(int n, const float *__restrict__ a
     for (int i = 0; i < n; ++i) {
         const float q = (i > 0) ? b2f[i - 1] * pm2 : 0.f;
         float p = fmaf(af[i] - sigma, pm1, -q);
-        if (p == 0.f) p = -pm1 * 0x1p-30f;
-        const int sc = __float_as_int(p) < 0 ? 1 : 0;
+        const bool z = (p == 0.f); // zero pivot: negative, p_i = 0 kept (see negcount_ldl)
+        const int sc = z ? (sp ^ 1) : (__float_as_int(p) < 0 ? 1 : 0);
         cnt += sc ^ sp;
         const int ex = (__float_as_int(p) >> 23) & 0xff;
-        if ((unsigned)(ex - (127 - 40)) > 80u) {
+        if ((unsigned)(ex - (127 - 40)) > 80u && !z) {
             const float s = __int_as_float((254 - ex) << 23); // 2^(127-ex)
             p *= s;
             pm1 *= s;

@@ -29,12 +29,18 @@ namespace mr3 {
 
 // ------------------------------------------------------------------ bisection
 
-// Sturm count at x for one node: double-float when the node's copy is exact enough and x
-// is representable (Ch. 5 x-bit eigenvalue approximation), else binary64.
+// Whether a count of node N at x runs in double-float.
+__device__ __forceinline__ bool node_df(const Node &N, double x) {
+    return N.dfok && df_shift_ok(scalbn(x, N.dfexp));
+}
+
+// Sturm count at x for one node: double-float on the node's scaled copy when that is
+// usable (Ch. 5 x-bit eigenvalue approximation), else binary64.
 __device__ __forceinline__ int node_count(const Node &N, int n, const double *__restrict__ rep,
                                           double x) {
-    if (N.dfok && df_safe(x)) {
-        const int k = negcount_df(n, (const float4 *)(rep + rep_df_offset(n)), df_from(x));
+    if (node_df(N, x)) {
+        const int k = negcount_df(n, (const float4 *)(rep + rep_df_offset(n)),
+                                  df_from(scalbn(x, N.dfexp)));
         if (k >= 0) return k;
     }
     return negcount_ldl(n, rep, rep + 2 * n, x);
@@ -52,8 +58,9 @@ __device__ __forceinline__ int node_count(const Node &N, int n, const double *__
 // paper's factor nu = 10 k_rr n eps, k_rr = 10 ((lambda (1 -+ nu) - tau)(1 -+ nu), end of
 // Sec. 3.2.3), then by powers of 2^8.
 //
-// Counts in double-float are exact for a relative perturbation of the representation of
-// a few units of 2^-47, so the final interval is widened by 32 n 2^-47 relative.
+// Counts in double-float (on the node's copy scaled by 2^dfexp, where every binary32
+// product stays normal) are exact for a relative perturbation of the representation of a
+// few units of 2^-47, so the final interval is widened by 32 n 2^-47 relative.
 __global__ void k_bisect2(int ngroups, const int *__restrict__ list, int L, int mtotal,
                           const int *__restrict__ cnode, const Node *__restrict__ nodes,
                           const BlkDesc *__restrict__ blks, const double *__restrict__ pool,
@@ -157,7 +164,7 @@ __global__ void k_bisect2(int ngroups, const int *__restrict__ list, int L, int 
         int cnt = 0;
         if (!done) {
             if (df_phase) {
-                used_df |= df_safe(x);
+                used_df |= node_df(N, x);
                 cnt = node_count(N, n, rep, x);
             } else {
                 cnt = negcount_ldl(n, rep, rep + 2 * n, x);
@@ -808,10 +815,8 @@ __global__ void k_shift(int ncluster, const ClusterItem *__restrict__ clusters,
     // double-float copy for the bisection
     const double *U = (win == 1) ? cdl : cd;
     const int kofs = (win == 1) ? 1 : 0;
-    float4 *cdf = (float4 *)(cd + rep_df_offset(n));
     double carry_u = 1.0;
     int carry_k = 0;
-    bool dfok = true;
     for (int base = 0; base < n; base += 32) {
         const int i = base + lane;
         const double ui = (i < n) ? U[i] : 1.0;
@@ -836,13 +841,11 @@ __global__ void k_shift(int ncluster, const ClusterItem *__restrict__ clusters,
                 cdl[i] = 0.0;
                 cdll[i] = 0.0;
             }
-            const dfloat a = df_from(dp), b = df_from(dllp);
-            cdf[i] = make_float4(a.h, a.l, b.h, b.l);
-            dfok &= df_safe(dp) && df_safe(dllp) && is_finite(dp) && is_finite(dllp);
         }
         __syncwarp();
     }
-    dfok = __all_sync(FULL_MASK, dfok);
+    int dfexp;
+    const bool dfok = df_write_copy_warp(n, cd, cdll, (float4 *)(cd + rep_df_offset(n)), dfexp);
     __syncwarp();
     build_prefix(n, cd);
 
@@ -859,6 +862,7 @@ __global__ void k_shift(int ncluster, const ClusterItem *__restrict__ clusters,
         Cn.c1 = q;
         Cn.depth = P.depth + 1;
         Cn.dfok = dfok ? 1 : 0;
+        Cn.dfexp = dfexp;
         Cn.sigma = P.sigma + tau;
         Cn.lnb = C.lnb - tau;
         Cn.rnb = C.rnb - tau;

@@ -42,11 +42,13 @@ __device__ int negcount_T_f64(int n, const double *__restrict__ d, const double 
         double q = 0.0;
         if (i > 0) { const double b = __ldg(e + i - 1); q = (b * b) * pm2; }
         double p = fma(ai, pm1, -q);
-        if (is_zero(p)) p = -pm1 * 0x1p-80;
-        const int sc = sign_bit(p);
+        // zero pivot: negative (the limit x -> x+), p_i = 0 kept; the next step then gives
+        // p_{i+1} = -beta_i^2 p_{i-1}, the pivot +infinity
+        const bool z = is_zero(p);
+        const int sc = z ? (sp ^ 1) : sign_bit(p);
         cnt += sc ^ sp;
         const int ex = biased_exp(p);
-        if ((unsigned)(ex - (1023 - 200)) > 400u) {
+        if ((unsigned)(ex - (1023 - 200)) > 400u && !z) {
             const double s = pow2i(1023 - ex);
             p *= s;
             pm1 *= s;
@@ -226,6 +228,7 @@ __global__ void k_blocks_from_flags(long long nrows, const int *flags, const int
     B.n = 0;
     B.rep = (long long)kRepStride * i + (long long)kRepPad * id;
     B.dfok = 0;
+    B.dfexp = 0;
     B.j0 = 1;
     B.j1 = 0;
     B.col0 = 0;
@@ -546,8 +549,6 @@ __global__ void k_root(int nblk, BlkDesc *blks, const double *__restrict__ D,
     }
     __syncwarp();
     const double xi = 8.0 * kEps;
-    float4 *rdf = (float4 *)(reg0 + rep_df_offset(n));
-    bool dfok = true;
     // pivots d_i = p_i / (p_{i-1} 2^k_{i-1}), by chunks of 32 (the previous chunk's last p
     // and exponent carried in registers: the chunk's writes reuse the slots it read)
     double carry_p = 1.0;
@@ -576,15 +577,12 @@ __global__ void k_root(int nblk, BlkDesc *blks, const double *__restrict__ D,
         reg0[i] = dp;
         reg1[i] = dl;
         reg2[i] = dll;
-        const dfloat a = df_from(dp), bb = df_from(dll);
-        rdf[i] = make_float4(a.h, a.l, bb.h, bb.l);
-        dfok &= df_safe(dp) && df_safe(dll);
     }
-    __syncwarp();
-    dfok = __all_sync(FULL_MASK, dfok);
+    int dfexp;
+    const bool dfok = df_write_copy_warp(n, reg0, reg2, (float4 *)(reg0 + rep_df_offset(n)), dfexp);
     __syncwarp();
     build_prefix(n, reg0);
-    if (lane == 0) { blks[b].mu = mu; blks[b].dfok = dfok ? 1 : 0; }
+    if (lane == 0) { blks[b].mu = mu; blks[b].dfok = dfok ? 1 : 0; blks[b].dfexp = dfexp; }
 }
 
 void launch_root(int nblk, BlkDesc *blks, const double *d, const double *e, double *pool0,
@@ -611,6 +609,7 @@ __global__ void k_init_columns(int nblk, const BlkDesc *__restrict__ blks, Node 
         N.c1 = B.col0 + m - 1;
         N.depth = 0;
         N.dfok = B.dfok;
+        N.dfexp = B.dfexp;
         N.sigma = B.mu;
         N.lnb = -INFINITY;
         N.rnb = INFINITY;

@@ -209,7 +209,9 @@ __global__ void __launch_bounds__(32) k_rqi(int nsingle, const SingleItem *__res
                     if (!bw && i == fend && !need_last) break;
                     const double qY = qi * Y;
                     double Xn = fma(pi, X, Y);
-                    if (is_zero(Xn)) Xn = -X * 0x1p-80;
+                    // an exactly zero pivot becomes a negative one 2^-80 times the
+                    // cancelled term |pi X| = |Y|: tiny relative to the data at any scale
+                    if (is_zero(Xn)) Xn = is_zero(Y) ? -X * 0x1p-80 : copysign(fabs(Y) * 0x1p-80, -X);
                     const int sc = sign_bit(Xn);
                     if (bw || full || i < r) cnt += sc ^ sp;
                     if (!bw && i == n - 1) { c_last = Xn; cprev_last = X; break; }

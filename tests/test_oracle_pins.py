@@ -129,6 +129,23 @@ def test_sturm_counts_between_eigenvalues(kind, n):
     assert oracle.negcount(d, e, w[-1] + 1.0) == n
 
 
+@pytest.mark.parametrize("scale", [1.0, 1e-30, 1e30])
+@pytest.mark.parametrize("n", [60, 61])
+def test_sturm_count_at_an_exactly_zero_pivot(n, scale):
+    # T = s (I + 1e-12 J): at sigma = s the first pivot is exactly zero.  The spectrum
+    # s (1 + 2e-12 cos(k pi / (n + 1))) is symmetric about s; for odd n, s itself is the
+    # middle eigenvalue.  The count of eigenvalues strictly below s is floor(n / 2) either
+    # way; just above s (closer than the nearest eigenvalue s (1 + ~5e-14)) it is
+    # ceil(n / 2).
+    d, e = np.full(n, scale), np.full(n - 1, 1e-12 * scale)
+    assert oracle.negcount(d, e, scale) == n // 2
+    assert oracle.negcount(d, e, scale * (1.0 + 1e-14)) == n - n // 2
+    w = oracle.eigvals(d, e)
+    k = np.arange(1, n + 1)
+    wt = np.sort(scale * (1.0 + 2e-12 * np.cos(np.pi * k / (n + 1))))
+    assert np.max(np.abs(w - wt)) <= 4 * n * EPS * scale
+
+
 @pytest.mark.parametrize("kind,n", [("random", 300), ("glued_wilkinson", 210)])
 def test_against_lapack(kind, n):
     # numpy.linalg.eigvalsh (LAPACK, a different algorithm) as an outside reference.
