@@ -218,6 +218,15 @@ int mr3_stemr_static(int n, const double *d, const double *e, int range, double 
                      int il, int iu, int *m, double *w, double *Z, int ldz,
                      const mr3_opts *opts, mr3_info *info, void *stream);
 
+/* Device memory.  The workspaces of mr3_stemr, mr3_stemr_host, mr3_stemr_batched and
+ * mr3_backward come from a stream-ordered memory pool that the library keeps per device,
+ * created on the first call made with that device current.  Memory a call frees stays in
+ * the pool for the next call instead of going back to the driver at each synchronisation
+ * (re-mapping several GB per call costs tens of ms).  mr3_release_memory returns the
+ * unused memory of every pool to the driver; memory still held by calls in flight stays.
+ * Thread-safe; returns MR3_SOK, or MR3_ECUDA if a CUDA call failed. */
+int mr3_release_memory(void);
+
 /* Message for a return code (static string). */
 const char *mr3_strerror(int code);
 

@@ -87,6 +87,8 @@ def lib():
             L.mr3_strerror.restype = ctypes.c_char_p
             L.mr3_version.argtypes = []
             L.mr3_version.restype = ctypes.c_char_p
+            L.mr3_release_memory.argtypes = []
+            L.mr3_release_memory.restype = c_int
             _lib = L
     return _lib
 
@@ -326,3 +328,11 @@ def eigh_tridiagonal(d, e):
 
 def version() -> str:
     return lib().mr3_version().decode()
+
+
+def release_memory() -> None:
+    """Return the unused device memory of the library's workspace pools to the driver
+    (the pools otherwise keep it for later calls)."""
+    rc = lib().mr3_release_memory()
+    if rc != 0:
+        raise RuntimeError("mr3_release_memory: " + lib().mr3_strerror(rc).decode())

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 #include "mr3.h"
 #include "mr3_kernels.h"
@@ -106,6 +107,46 @@ struct Prof {
     }
 };
 
+} // namespace
+
+// ------------------------------------------------------------------ memory pool
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mutex;
+cudaMemPool_t g_pools[kMaxDevices] = {};
+} // namespace
+
+cudaError_t lib_malloc_async(void **p, size_t bytes, cudaStream_t s) {
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    if (dev < 0 || dev >= kMaxDevices) return cudaMallocAsync(p, bytes, s);
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mutex);
+        pool = g_pools[dev];
+        if (!pool) {
+            cudaMemPoolProps props;
+            memset(&props, 0, sizeof(props));
+            props.allocType = cudaMemAllocationTypePinned;
+            props.handleTypes = cudaMemHandleTypeNone;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+                cudaGetLastError();
+                return cudaMallocAsync(p, bytes, s);
+            }
+            unsigned long long keep = ~0ull; // never trimmed at synchronisation
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+            g_pools[dev] = pool;
+        }
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+namespace {
+
 // Stream-ordered workspace: every block is returned (cudaFreeAsync) when the call ends.
 struct Workspace {
     cudaStream_t s;
@@ -115,7 +156,7 @@ struct Workspace {
     template <class T> T *get(size_t count) {
         void *p = nullptr;
         const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
-        if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+        if (lib_malloc_async(&p, bytes, s) != cudaSuccess) {
             cudaGetLastError();
             oom = true;
             return nullptr;
@@ -285,24 +326,35 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
     int ncur = nblk;
     double *scratch = nullptr;
     size_t scratch_len = 0; // doubles
-    const long long scratch_cap_bytes = 2ll << 30; // RQI scratch budget per launch
+    // RQI scratch budget per launch: enough for every root-level singleton of a few
+    // n = 8192 matrices to run at once with teams of 2 (~10 warps per SM), where the
+    // latency of the scratch and representation loads is hidden by other warps; the slot
+    // count is halved while the allocation fails
+    const long long scratch_cap_bytes = 8ll << 30;
     int status = 0;
     auto run_singles = [&](int level, const LevelCounters &hc) -> int {
         const int team = dd ? 0 : rqi_team(hc.nsingle, nmat);
         long long slots = dd ? rqi_dd_threads(hc.nsingle, nmax, 2 * scratch_cap_bytes)
                              : rqi_slots(hc.nsingle, nmax, scratch_cap_bytes, team);
         const size_t per_slot = dd ? (size_t)4 * nmax : (size_t)rqi_scratch_per_index(team) * nmax;
-        const size_t need = (size_t)slots * per_slot;
-        if (need > scratch_len) {
+        if ((size_t)slots * per_slot > scratch_len) {
             if (scratch) cudaFreeAsync(scratch, side); // after the side stream's last use
-            void *p = nullptr;
-            if (cudaMallocAsync(&p, need * sizeof(double), s) != cudaSuccess) {
+            scratch = nullptr;
+            scratch_len = 0;
+            for (;;) {
+                const size_t need = (size_t)slots * per_slot;
+                void *p = nullptr;
+                if (lib_malloc_async(&p, need * sizeof(double), s) == cudaSuccess) {
+                    scratch = (double *)p;
+                    scratch_len = need;
+                    break;
+                }
                 cudaGetLastError();
-                scratch = nullptr;
-                return MR3_EOOM;
+                // binary64 teams: at least one warp per SM; double-double: whole blocks of 128
+                const long long minslots = dd ? 128 : 152;
+                if (slots <= minslots) return MR3_EOOM;
+                slots = std::max<long long>(minslots, dd ? (slots / 2) / 128 * 128 : slots / 2);
             }
-            scratch = (double *)p;
-            scratch_len = need;
         }
         cudaEvent_t ready = guard.make();
         cudaEventRecord(ready, s);
@@ -510,10 +562,10 @@ int mr3_stemr_host(int n, const double *d, const double *e, int range, double vl
     cudaStream_t s = (cudaStream_t)stream;
     double *dd = nullptr, *de = nullptr, *dw = nullptr, *dz = nullptr;
     int rc = 0;
-    if (cudaMallocAsync((void **)&dd, sizeof(double) * n, s) != cudaSuccess ||
-        cudaMallocAsync((void **)&de, sizeof(double) * std::max(1, n - 1), s) != cudaSuccess ||
-        cudaMallocAsync((void **)&dw, sizeof(double) * n, s) != cudaSuccess ||
-        cudaMallocAsync((void **)&dz, sizeof(double) * (size_t)n * n, s) != cudaSuccess) {
+    if (lib_malloc_async((void **)&dd, sizeof(double) * n, s) != cudaSuccess ||
+        lib_malloc_async((void **)&de, sizeof(double) * std::max(1, n - 1), s) != cudaSuccess ||
+        lib_malloc_async((void **)&dw, sizeof(double) * n, s) != cudaSuccess ||
+        lib_malloc_async((void **)&dz, sizeof(double) * (size_t)n * n, s) != cudaSuccess) {
         cudaGetLastError();
         rc = MR3_EOOM;
     }
@@ -607,5 +659,16 @@ const char *mr3_strerror(int code) {
 }
 
 const char *mr3_version(void) { return "mr3-gb300 0.1 sm_103a"; }
+
+int mr3_release_memory(void) {
+    std::lock_guard<std::mutex> lock(g_pool_mutex);
+    int rc = MR3_SOK;
+    for (int dev = 0; dev < kMaxDevices; ++dev)
+        if (g_pools[dev] && cudaMemPoolTrimTo(g_pools[dev], 0) != cudaSuccess) {
+            cudaGetLastError();
+            rc = MR3_ECUDA;
+        }
+    return rc;
+}
 
 } // extern "C"

@@ -27,7 +27,7 @@
 #include <mutex>
 #include <cublas_v2.h>
 #include "mr3.h"
-#include "mr3_internal.cuh"
+#include "mr3_kernels.h"
 
 namespace mr3 {
 namespace {
@@ -361,12 +361,12 @@ int vector_part_ozaki(int n, const double *w, const double *Z, int ldz, const do
         if (mx) cudaFreeAsync(mx, st);
         return code;
     };
-    if (cudaMallocAsync((void **)&SA, sizeof(unsigned short) * plane * pl.s, st) != cudaSuccess ||
-        cudaMallocAsync((void **)&SB, sizeof(unsigned short) * plane * pl.s, st) != cudaSuccess ||
-        cudaMallocAsync((void **)&Cbuf, sizeof(float) * plane * pl.s, st) != cudaSuccess ||
-        cudaMallocAsync((void **)&acc, sizeof(double) * plane, st) != cudaSuccess ||
-        cudaMallocAsync((void **)&ex, sizeof(int) * 4 * n, st) != cudaSuccess ||
-        cudaMallocAsync((void **)&mx, sizeof(unsigned long long) * 4 * n, st) != cudaSuccess) {
+    if (lib_malloc_async((void **)&SA, sizeof(unsigned short) * plane * pl.s, st) != cudaSuccess ||
+        lib_malloc_async((void **)&SB, sizeof(unsigned short) * plane * pl.s, st) != cudaSuccess ||
+        lib_malloc_async((void **)&Cbuf, sizeof(float) * plane * pl.s, st) != cudaSuccess ||
+        lib_malloc_async((void **)&acc, sizeof(double) * plane, st) != cudaSuccess ||
+        lib_malloc_async((void **)&ex, sizeof(int) * 4 * n, st) != cudaSuccess ||
+        lib_malloc_async((void **)&mx, sizeof(unsigned long long) * 4 * n, st) != cudaSuccess) {
         cudaGetLastError();
         return done(MR3_EOOM);
     }
@@ -430,9 +430,9 @@ extern "C" int mr3_backward(int n, int k, const double *w, const double *Z, int 
         if (code == 0 && cudaStreamSynchronize(s) != cudaSuccess) { cudaGetLastError(); return (int)MR3_ECUDA; }
         return code;
     };
-    if (cudaMallocAsync((void **)&part, sizeof(double) * 2 * kRowChunks * (size_t)n, s) != cudaSuccess ||
-        (vec && cudaMallocAsync((void **)&Y, sizeof(double) * (size_t)n * n, s) != cudaSuccess) ||
-        (vec && n < kOzakiMinN && cudaMallocAsync((void **)&C, sizeof(double) * (size_t)n * n, s) != cudaSuccess)) {
+    if (lib_malloc_async((void **)&part, sizeof(double) * 2 * kRowChunks * (size_t)n, s) != cudaSuccess ||
+        (vec && lib_malloc_async((void **)&Y, sizeof(double) * (size_t)n * n, s) != cudaSuccess) ||
+        (vec && n < kOzakiMinN && lib_malloc_async((void **)&C, sizeof(double) * (size_t)n * n, s) != cudaSuccess)) {
         cudaGetLastError();
         return done(MR3_EOOM);
     }

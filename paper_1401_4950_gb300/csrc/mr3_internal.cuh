@@ -192,8 +192,11 @@ __device__ __forceinline__ void negcount_ldl2(int n, const double *__restrict__ 
                                               double s1, int &k0, int &k1) {
     double a0 = -s0, c0 = 1.0, a1 = -s1, c1 = 1.0;
     int p0 = 0, p1 = 0, n0 = 0, n1 = 0;
+    double dn = __ldg(d), ln = (n > 1) ? __ldg(dll) : 0.0; // prefetched data of step i
     for (int i = 0; i < n - 1; ++i) {
-        const double di = __ldg(d + i), li = __ldg(dll + i);
+        const double di = dn, li = ln;
+        dn = __ldg(d + i + 1);
+        ln = (i + 1 < n - 1) ? __ldg(dll + i + 1) : 0.0;
         const double t0 = li * a0, t1 = li * a1;
         double x0 = fma(di, c0, a0), x1 = fma(di, c1, a1);
         const bool z0 = is_zero(x0), z1 = is_zero(x1);
@@ -207,7 +210,7 @@ __device__ __forceinline__ void negcount_ldl2(int n, const double *__restrict__ 
         if ((unsigned)(e1 - (1023 - 200)) > 400u && !z1) { const double s = pow2i(1023 - e1); x1 *= s; a1 *= s; }
         c0 = x0; c1 = x1; p0 = q0; p1 = q1;
     }
-    double x0 = fma(__ldg(d + n - 1), c0, a0), x1 = fma(__ldg(d + n - 1), c1, a1);
+    double x0 = fma(dn, c0, a0), x1 = fma(dn, c1, a1);
     n0 += (is_zero(x0) ? (p0 ^ 1) : sign_bit(x0)) ^ p0;
     n1 += (is_zero(x1) ? (p1 ^ 1) : sign_bit(x1)) ^ p1;
     k0 = n0;

@@ -65,6 +65,11 @@ void launch_shift(int ncluster, const ClusterItem *clusters, const long long *cl
                   Node *child_nodes, double *child_tau, int *cnode, int *active_list,
                   const int *jloc, double *lo, double *hi, int max_tries, unsigned fault_mask,
                   double2 *tri, void *ws, DevInfo *info, cudaStream_t s);
+// Stream-ordered allocation from the library's memory pool of the current device (one
+// pool per device whose release threshold keeps freed memory for later calls); free with
+// cudaFreeAsync.
+cudaError_t lib_malloc_async(void **p, size_t bytes, cudaStream_t s);
+
 // Bytes of the ws scratch launch_shift needs for ncluster clusters.
 size_t shift_scratch_bytes(int ncluster, int max_tries);
 // Ascending eigenvalues: running-maximum fix for single-block matrices, flags for the rest.

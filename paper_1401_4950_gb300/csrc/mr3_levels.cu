@@ -23,6 +23,12 @@ namespace mr3 {
 #define MR3_REFINE1_LANES_PER_SM 128
 #endif
 
+// Relative width at which the double-float phase of the cluster-end refinement stops.
+#ifndef MR3_REFINE_DF_RTOL
+#define MR3_REFINE_DF_RTOL 1e-13
+#endif
+constexpr double kRefineDfRtol = MR3_REFINE_DF_RTOL;
+
 #ifndef MR3_TAU_OFFSET
 #define MR3_TAU_OFFSET 100.0
 #endif
@@ -408,8 +414,10 @@ void launch_classify(int nnode, const Node *nodes, const BlkDesc *blks, const do
 // leaves that end well separated in the child) or at full accuracy (4 eps |lambda|).  The
 // bound starts from the neighbour's interval and tightens with every sample whose count
 // shows the neighbour on its far side.  Two launches: phase 0 counts in double-float and
-// stops at 1e-11 relative width (the limit of its counts), phase 1 continues in binary64
-// with fewer lanes per end (the binary64 pipe, not latency, bounds it when ends are many).
+// stops at 1e-13 relative width (near the practical accuracy of its counts on the scaled
+// copy), phase 1 checks those bounds with binary64 counts, widens where they fail, and
+// continues in binary64 with fewer lanes per end (the binary64 pipe, not latency, bounds
+// it when ends are many).
 __global__ void k_refine_ends(int ncluster, const ClusterItem *__restrict__ clusters,
                               const Node *__restrict__ nodes, const BlkDesc *__restrict__ blks,
                               const double *__restrict__ pool, const int *__restrict__ jloc,
@@ -464,9 +472,13 @@ __global__ void k_refine_ends(int ncluster, const ClusterItem *__restrict__ clus
             const bool ok = okL && okH;
             if (__all_sync(0xffffffffu, ok || !active)) break;
             if (active && !ok) {
-                const double f = ldexp(kap, 4 * attempt);
-                if (!okL) L -= f * fmax(fabs(L), kSafmin);
-                if (!okH) H += f * fmax(fabs(H), kSafmin);
+                // geometric from the interval's own width up to the copy's error bound
+                // kap (16^attempt), then beyond it
+                const double w0 = fmax(H - L, kEps * fmax(fabs(L), fabs(H)));
+                const double f = fmin(ldexp(w0, 4 * (attempt + 1)),
+                                      ldexp(kap, 4 * attempt) * fmax(fmax(fabs(L), fabs(H)), kSafmin));
+                if (!okL) L -= f;
+                if (!okH) H += f;
             }
         }
     }
@@ -474,7 +486,7 @@ __global__ void k_refine_ends(int ncluster, const ClusterItem *__restrict__ clus
         const double w = H - L;
         const double gap_lb = side ? (L - nb) : (nb - H);
         double tol = fmax(4.0 * kEps * fmax(fabs(L), fabs(H)), 1e-3 * fmax(gap_lb, 0.0));
-        if (phase == 0) tol = fmax(tol, 1e-11 * fmax(fabs(L), fabs(H)));
+        if (phase == 0) tol = fmax(tol, kRefineDfRtol * fmax(fabs(L), fabs(H)));
         bool done = !active || !(w > tol);
         const double x = L + (k + 1) * (w / (E + 1));
         if (__ballot_sync(0xffffffffu, !(x > L && x < H)) & gmask) done = true;

@@ -152,6 +152,18 @@ def test_deterministic(cuda):
     assert np.array_equal(w1, w2) and np.array_equal(Z1, Z2)
 
 
+def test_release_memory_between_calls(cuda):
+    # the workspace pool keeps memory between calls; handing it back to the driver does not
+    # change the next call's result
+    import paper_1401_4950_gb300 as mr3
+    d, e = tm.random_uniform(800, 31, 32)
+    w1, Z1, _ = _solve(d, e)
+    mr3.release_memory()
+    w2, Z2, _ = _solve(d, e)
+    mr3.release_memory()
+    assert np.array_equal(w1, w2) and np.array_equal(Z1, Z2)
+
+
 def test_fault_injection_rqi_fallback(cuda):
     import paper_1401_4950_gb300 as mr3
     d, e = tm.random_uniform(300, 41, 42)
