@@ -145,6 +145,63 @@ cudaError_t lib_malloc_async(void **p, size_t bytes, cudaStream_t s) {
     return cudaMallocFromPoolAsync(p, bytes, pool, s);
 }
 
+// ------------------------------------------------------------------ counter read-back
+
+namespace {
+
+// Counters the host reads between launches (the level's singleton and cluster counts, the
+// matrix descriptors, the statistics) travel without a copy engine: a small kernel stores
+// them into mapped pinned host memory, and the host reads them once the stream has
+// synchronised.  A cudaMemcpyAsync to the host would queue behind any large transfer the
+// caller has in flight on the same copy engine (a 1.6 GB read of a previous result held
+// every tree level's read for its full duration).  One growing buffer per host thread;
+// with unified addressing its host address is also its device address.
+struct MappedBuffer {
+    void *h = nullptr;
+    size_t bytes = 0;
+};
+thread_local MappedBuffer t_mapped;
+
+__global__ void k_publish(const unsigned *__restrict__ src, unsigned *dst, size_t words) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < words;
+         i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+} // namespace
+
+// Copies bytes (a multiple of 4) from device memory to host memory in stream order and
+// waits for them.
+cudaError_t read_back(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return cudaSuccess;
+    if (bytes % 4 != 0) {
+        cudaError_t err = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s);
+        return err != cudaSuccess ? err : cudaStreamSynchronize(s);
+    }
+    if (t_mapped.bytes < bytes) {
+        if (t_mapped.h) cudaFreeHost(t_mapped.h);
+        t_mapped = MappedBuffer();
+        const size_t want = std::max<size_t>(bytes, 64 << 10);
+        void *h = nullptr;
+        cudaError_t err = cudaHostAlloc(&h, want, cudaHostAllocMapped | cudaHostAllocPortable);
+        if (err != cudaSuccess) return err;
+        t_mapped.h = h;
+        t_mapped.bytes = want;
+    }
+    void *dptr = nullptr;
+    cudaError_t err = cudaHostGetDevicePointer(&dptr, t_mapped.h, 0);
+    if (err != cudaSuccess) return err;
+    const size_t words = bytes / 4;
+    const unsigned blocks = (unsigned)std::min<size_t>((words + 255) / 256, 64);
+    k_publish<<<blocks, 256, 0, s>>>((const unsigned *)src, (unsigned *)dptr, words);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    err = cudaStreamSynchronize(s);
+    if (err != cudaSuccess) return err;
+    memcpy(dst, t_mapped.h, bytes);
+    return cudaSuccess;
+}
+
 namespace {
 
 // Stream-ordered workspace: every block is returned (cudaFreeAsync) when the call ends.
@@ -221,8 +278,7 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
     launch_exclusive_scan(flags, scanned, nrows, dint + 1, scan_tmp, s);
     prof.end(tk, 0, 5);
     int hint[4];
-    CK(cudaMemcpyAsync(hint, dint, sizeof(hint), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    CK(read_back(hint, dint, sizeof(hint), s));
     if (hint[0]) {
         for (auto &M : mats) M.m = 0;
         out.status_counts[MR3_SNONFINITE] = 1;
@@ -238,8 +294,7 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
     if (range == MR3_RANGE_INDEX) launch_index_multi(nmat, dmats, blks, d, e, s);
     launch_assign_columns(nmat, dmats, blks, range, s);
     prof.end(tk, 0, range == MR3_RANGE_INDEX ? 6 : 5);
-    CK(cudaMemcpyAsync(mats.data(), dmats, sizeof(MatDesc) * nmat, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    CK(read_back(mats.data(), dmats, sizeof(MatDesc) * nmat, s));
     ws.release(flags);
     ws.release(scanned);
     ws.release(scan_tmp);
@@ -383,8 +438,7 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
                         clusters, crep, cnode, ctr, dinfo, s);
         prof.end(tk, 3, 1);
         LevelCounters hc;
-        CK(cudaMemcpyAsync(&hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
+        CK(read_back(&hc, ctr, sizeof(hc), s));
         cudaEvent_t level_rqi = nullptr;
         if (hc.nsingle > 0) {
             const int rc = run_singles(level, hc);
@@ -438,8 +492,7 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
             CK(cudaMemsetAsync(ctr, 0, sizeof(LevelCounters), s));
             launch_classify(ncur, cur_nodes, blks, lo, hi, -1e308, gapl, gapr, singles2[lv & 1],
                             clusters, crep, cnode, ctr, dinfo, s);
-            CK(cudaMemcpyAsync(&hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
+            CK(read_back(&hc, ctr, sizeof(hc), s));
             if (hc.nsingle > 0) {
                 const int rc = run_singles(lv, hc);
                 if (rc) return rc;
@@ -460,8 +513,7 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
     launch_order_flags(nmat, dmats, w, oflags, s);
     prof.end(tk, 7, 1);
     std::vector<int> hflags(nmat);
-    CK(cudaMemcpyAsync(hflags.data(), oflags, sizeof(int) * nmat, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    CK(read_back(hflags.data(), oflags, sizeof(int) * nmat, s));
     for (int b = 0; b < nmat; ++b) {
         const MatDesc &M = mats[b];
         if (hflags[b] && M.m > 1) {
@@ -475,8 +527,7 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
         }
     }
     DevInfo hi_info;
-    CK(cudaMemcpyAsync(&hi_info, dinfo, sizeof(hi_info), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    CK(read_back(&hi_info, dinfo, sizeof(hi_info), s));
     CK(cudaGetLastError());
     out.dmax = hi_info.dmax;
     out.nclusters = hi_info.nclusters;
