@@ -48,9 +48,15 @@ CONFIGS = {
 }
 
 
-def _matrices(cfg):
+def _workload(cfg, n_override=None):
+    w = CONFIGS[cfg]["workload"]
+    return w if not n_override else w + " (matrix order overridden: n=%d)" % n_override
+
+
+def _matrices(cfg, n_override=None):
     out = []
     for kind, n, seeds in CONFIGS[cfg]["mats"]:
+        n = n_override or n
         if kind == "random":
             d, e = tm.random_uniform(n, *seeds)
         else:
@@ -150,7 +156,7 @@ def cpu_baseline(mats, budget_s=15.0):
 def run_reference(args, cfg, rank):
     if rank != 0:
         return
-    mats = _matrices(cfg)
+    mats = _matrices(cfg, args.n)
     budget = max(2.0, 150.0 / (args.steps + args.warmup))
     per, _, _ = calibrate_sample(mats, budget)
     for _ in range(args.warmup):
@@ -165,7 +171,7 @@ def run_reference(args, cfg, rank):
             "unit": "eigenpairs/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": CONFIGS[cfg]["workload"],
+            "data": "synthetic", "config": {"workload": _workload(cfg, args.n),
                                             "sample_per_matrix": per},
             "cpu_baseline": {"value": value, "unit": "eigenpairs/s", "cores": 1,
                              "kind": "oracle",
@@ -206,7 +212,7 @@ def run_gpu(args, cfg, rank, world):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    mats = _matrices(cfg)
+    mats = _matrices(cfg, args.n)
     dev_mats = [(k, torch.tensor(d, device=dev), torch.tensor(e, device=dev)) for k, d, e in mats]
     units_per_step = sum(len(d) for _, d, _ in mats)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -369,7 +375,7 @@ def run_gpu(args, cfg, rank, world):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": CONFIGS[cfg]["workload"],
+            "config": {"workload": _workload(cfg, args.n),
                        "n": [len(d) for _, d, _ in mats],
                        "matrices_per_step": len(mats), "l2": "flushed between steps "
                        "(256 MiB device write outside the per-step events)",
@@ -525,6 +531,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mr3", choices=["mr3", "reference"])
     ap.add_argument("--config", default="c2", choices=sorted(CONFIGS))
+    ap.add_argument("--n", type=int, default=None,
+                    help="matrix order instead of the config's (smaller cases for ncu captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--batched", action="store_true",
