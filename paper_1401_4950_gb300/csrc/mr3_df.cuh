@@ -106,16 +106,16 @@ __device__ __forceinline__ double df_to(dfloat x) { return (double)x.h + (double
 // (a, c) rescaled down to 2^-40, the error words fall to the subnormal range and carry
 // ~2^-42 relative precision, 64 times the bound the bisection widens by.  Sturm counts
 // do not change when d, dll and sigma are scaled by one power of two, so the copy of each
-// representation holds 2^k (d, dll) with its largest entry in [2^20, 2^21), and the count
-// runs at 2^k sigma.  A copy is used only when every scaled pivot is at least 2^-46 (with
+// representation holds 2^k (d, dll) with its largest entry in [1, 2), and the count runs
+// at 2^k sigma.  A copy is used only when every scaled pivot is at least 2^-46 (with
 // |c| >= 2^-40 the products d_i c_{i-1} then stay above 2^-86, and a binary32 product
 // and its TwoProd error word are exact down to ~2^-101) and every nonzero scaled dll_i
 // at least 2^-100 (its double-float tail normal); otherwise the node counts in binary64.
-// On the other side, the largest entry at 2^21 keeps sigma c below 2^120 after the jump
-// of c at a pivot as small as that.
-constexpr int kDfTopExp = 20;
+// Entries of order one also keep the growth of c over a few unrolled steps far from the
+// binary32 overflow.
+constexpr int kDfTopExp = 0;
 
-// k with amax 2^k in [2^20, 2^21) (amax > 0 and finite).
+// k with amax 2^k in [1, 2) (amax > 0 and finite).
 __device__ __forceinline__ int df_scale_exp(double amax) {
     int e;
     (void)frexp(amax, &e); // amax in [2^(e-1), 2^e)
@@ -128,8 +128,12 @@ __device__ __forceinline__ bool df_entry_ok(double ds, double dlls) {
     return a >= 0x1p-46 && a <= 0x1p100 && (b == 0.0 || (b >= 0x1p-100 && b <= 0x1p100));
 }
 
-// A scaled shift usable in double-float (a tiny one loses only bits far below the data's).
-__device__ __forceinline__ bool df_shift_ok(double xs) { return fabs(xs) <= 0x1p100; }
+// A scaled shift usable in double-float: zero, or in [2^-80, 2^100] (see the magnitudes
+// of the count below).
+__device__ __forceinline__ bool df_shift_ok(double xs) {
+    const double a = fabs(xs);
+    return a == 0.0 || (a >= 0x1p-80 && a <= 0x1p100);
+}
 
 // Writes the scaled copy of the representation with pivots d[0..n) and dll[0..n-1) to
 // out[0..n) (float4 {d.h, d.l, dll.h, dll.l}; dll_{n-1} = 0), warp-collective.  Returns
@@ -182,40 +186,105 @@ __device__ __forceinline__ bool df_write_copy_serial(int n, const double *d, con
     return ok;
 }
 
+// Magnitudes.  c and a = s c share one scale, and s can be far below the data (s_1 =
+// -sigma, and s stays of the order of sigma along stretches of the chain when sigma is
+// tiny against the data).  So c is kept high, near 2^30 (rescaled when it leaves
+// [2^-10, 2^70]), and shifts below 2^-80 count in binary64 (df_shift_ok): then sigma c
+// >= 2^-90 and d_i c >= 2^-56, and in every sum of the recurrence the larger term keeps
+// exact TwoProd error words (normal down to ~2^-101).  With c near 1 instead, a and its
+// products fell below the binary32 range on a glued Wilkinson matrix at sigma ~ 2^-67
+// (relative), the error words flushed to zero and a count came out one too high.
+constexpr int kDfCExp = 30; // c is normalised to [2^30, 2^31)
+
+// One step of the double-float count with per-step rules: an exactly zero c_i counts as a
+// negative pivot (the limit sigma -> sigma+), (a, c) are rescaled to |c| in
+// [2^30, 2^31) when c leaves [2^-10, 2^70]; false when the recurrence left the binary32
+// range.
+__device__ __forceinline__ bool df_step_exact(const float4 q, bool last, dfloat ns, dfloat &a,
+                                              dfloat &cp, int &sp, int &cnt) {
+    dfloat c = df_fma({q.x, q.y}, cp, a);
+    const bool z = (c.h == 0.f);
+    const int sc = z ? (sp ^ 1) : (__float_as_int(c.h) < 0 ? 1 : 0);
+    cnt += sc ^ sp;
+    if (!last) {
+        a = df_dot2({q.z, q.w}, a, ns, c);
+        const int ex = (__float_as_int(c.h) >> 23) & 0xff;
+        if ((unsigned)(ex - (127 - 10)) > 80u && !z) {
+            if (ex == 0xff) return false;
+            // to [2^30, 2^31) in two exact factors: 2^(127-ex) (2^126 for a subnormal c),
+            // each representable, then 2^30
+            const float s1 = ex > 0 ? __int_as_float((254 - ex) << 23) : 0x1p126f;
+            const float s2 = __int_as_float((127 + kDfCExp) << 23);
+            c.h = __fmul_rn(__fmul_rn(c.h, s1), s2);
+            c.l = __fmul_rn(__fmul_rn(c.l, s1), s2);
+            a.h = __fmul_rn(__fmul_rn(a.h, s1), s2);
+            a.l = __fmul_rn(__fmul_rn(a.l, s1), s2);
+        }
+        if (!(fabsf(a.h) < 0x1p120f)) return false;
+    }
+    cp = c;
+    sp = sc;
+    return true;
+}
+
 // NegCount on L D L^T at sigma in double-float, homogeneous form (see negcount_ldl in
-// mr3_internal.cuh): c_i = d_i c_{i-1} + a_i, a_{i+1} = dll_i a_i - sigma c_i, with
-// (a, c) rescaled by a power of two when c leaves [2^-40, 2^40].  dd holds
-// {d.h, d.l, dll.h, dll.l} per index, scaled as above, and sigma carries the same scale.  Returns -1 if the recurrence left the binary32
+// mr3_internal.cuh): c_i = d_i c_{i-1} + a_i, a_{i+1} = dll_i a_i - sigma c_i.  dd holds
+// {d.h, d.l, dll.h, dll.l} per index, scaled as above, and sigma carries the same scale.
+// As in negcount_ldl, the serial loop has no data-dependent branch: blocks of 4 unrolled
+// steps (an exact zero pivot needs no test, its pair with the next pivot contributes one
+// negative either way), then (a, c) normalised by a power of two (measured on GB300: 108
+// cycles per step against 255 with the per-step rescale test).  A flag collected off the
+// recurrence marks a block in which c fell below 2^-10 (see the magnitudes above) or a
+// value left the range; such a block is redone with the per-step rules.  Returns -1 if the recurrence left the binary32
 // range (the caller then counts in binary64).
+__device__ __forceinline__ float df_norm_pow2(float c) {
+    const int ex = (__float_as_int(c) >> 23) & 0xff;
+    // called with |c| >= 2^-10 (ex >= 117) or an exact zero; other values left unscaled
+    return (ex >= 1 + kDfCExp && ex < 0xff) ? __int_as_float((254 + kDfCExp - ex) << 23) : 1.f;
+}
+
 __device__ __forceinline__ int negcount_df(int n, const float4 *__restrict__ dd, dfloat sigma) {
     const dfloat ns = df_neg(sigma);
-    dfloat a = ns, cp = {1.f, 0.f};
-    int sp = 0, cnt = 0;
+    const float c0s = __int_as_float((127 + kDfCExp) << 23); // 2^30
+    dfloat a = {__fmul_rn(ns.h, c0s), __fmul_rn(ns.l, c0s)}, cp = {c0s, 0.f};
+    int sp = 0, cnt = 0, i = 0;
     float4 qn = __ldg(dd); // prefetched data of step i
-    for (int i = 0; i < n; ++i) {
+    for (; i + 4 < n; i += 4) {
+        const dfloat a0 = a, c0 = cp;
+        const int sp0 = sp, cnt0 = cnt;
+        unsigned bad = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float4 q = qn;
+            qn = __ldg(dd + i + u + 1);
+            const dfloat c = df_fma({q.x, q.y}, cp, a);
+            const int sc = __float_as_int(c.h) < 0 ? 1 : 0;
+            cnt += sc ^ sp;
+            sp = sc;
+            a = df_dot2({q.z, q.w}, a, ns, c);
+            const int ex = (__float_as_int(c.h) >> 23) & 0xff;
+            bad |= ((unsigned)(ex - (127 - 10)) > 137u || !(fabsf(a.h) < 0x1p120f)) ? 1u : 0u;
+            cp = c;
+        }
+        if (__builtin_expect(bad != 0, 0)) {
+            a = a0;
+            cp = c0;
+            sp = sp0;
+            cnt = cnt0;
+            for (int k = i; k < i + 4; ++k)
+                if (!df_step_exact(__ldg(dd + k), false, ns, a, cp, sp, cnt)) return -1;
+        }
+        const float q = df_norm_pow2(cp.h);
+        cp.h = __fmul_rn(cp.h, q);
+        cp.l = __fmul_rn(cp.l, q);
+        a.h = __fmul_rn(a.h, q);
+        a.l = __fmul_rn(a.l, q);
+        if (!(fabsf(a.h) < 0x1p120f)) return -1;
+    }
+    for (; i < n; ++i) {
         const float4 q = qn;
         if (i + 1 < n) qn = __ldg(dd + i + 1);
-        const dfloat di = {q.x, q.y};
-        dfloat c = df_fma(di, cp, a);
-        const bool z = (c.h == 0.f); // zero pivot: negative, c_i = 0 kept (see negcount_ldl)
-        const int sc = z ? (sp ^ 1) : (__float_as_int(c.h) < 0 ? 1 : 0);
-        cnt += sc ^ sp;
-        if (i < n - 1) {
-            const dfloat dlli = {q.z, q.w};
-            a = df_dot2(dlli, a, ns, c);
-            const int ex = (__float_as_int(c.h) >> 23) & 0xff;
-            if ((unsigned)(ex - (127 - 40)) > 80u && !z) {
-                if (ex == 0xff) return -1;
-                const float s = __int_as_float((254 - ex) << 23); // 2^(127-ex)
-                c.h = __fmul_rn(c.h, s);
-                c.l = __fmul_rn(c.l, s);
-                a.h = __fmul_rn(a.h, s);
-                a.l = __fmul_rn(a.l, s);
-            }
-            if (!(fabsf(a.h) < 0x1p120f)) return -1;
-        }
-        cp = c;
-        sp = sc;
+        if (!df_step_exact(q, i == n - 1, ns, a, cp, sp, cnt)) return -1;
     }
     return cnt;
 }

@@ -147,40 +147,89 @@ __device__ __forceinline__ double splitmix_pm1(unsigned long long seed, unsigned
 // and sign(d+_i) = sign(c_i) xor sign(c_{i-1}).  Each rounding error can be pushed onto
 // d_i or dll_i as an O(eps) relative perturbation (the pair (a, c) only shares a
 // positive scale), so the count is exact for a relatively perturbed representation,
-// the property bisection on an RRR relies on.  (a, c) are rescaled by a power of two
-// when c leaves [2^-200, 2^200].  A pivot that is exactly zero counts as negative, the
-// limit sigma -> sigma+ (SignBit(-0) = 1, App. B remarks), and c_i = 0 is kept: the
-// homogeneous form needs no division, the next step gives c_{i+1} = dll_i a_i, and its
-// pivot d+_{i+1} = c_{i+1} / c_i is the limit +infinity, counted positive because
-// sign(c_{i+1}) = sign(c_{i-1}) xor 1 when dll_i and d_i share a sign.  A tiny substitute
-// pivot would have to be tiny relative to the data, which carry no fixed scale.  Critical
-// path: two dependent FMAs per step.
+// the property bisection on an RRR relies on.
+//
+// Zero pivots (App. B remarks: SignBit(-0) = 1).  The homogeneous form needs no division,
+// so an exactly zero c_i is simply kept: the next step gives c_{i+1} = dll_i a_i, the
+// pivot d+_{i+1} = c_{i+1} / c_i is infinite, and the pair (d+_i, d+_{i+1}) contributes
+// exactly one negative pivot whatever sign the zero carries (sign(c_{i+1}) =
+// sign(c_{i-1}) xor 1 when dll_i and d_i share a sign), which is the count of the limit
+// sigma -> sigma+ .  Only the last pivot has no successor: an exactly zero d+_{n-1}
+// counts as negative.  A tiny substitute pivot would have to be tiny relative to the
+// data, which carry no fixed scale.
+//
+// Scaling.  (a, c) must stay in the binary64 range.  A data-dependent branch inside the
+// serial loop costs ~380 cycles per step on GB300 (measured: 593 against 215 cycles per
+// step without it, whose two dependent FMAs are the critical path), so the loop runs in
+// blocks of 8 unrolled steps without a branch and normalises (a, c) by a power of two
+// at the end of each block.  A block whose end value left [2^-923, 2^877] (data of
+// extreme magnitude, or a pivot near underflow) is redone from its saved state with a
+// rescale after every step; the last steps run that way too.
+__device__ __forceinline__ double norm_pow2(double c) {
+    const int ex = biased_exp(c);
+    return (ex > 0 && ex < 0x7ff) ? pow2i(1023 - ex) : 1.0;
+}
+
+// One step with the per-step rules (used for redone blocks and the last steps).
+__device__ __forceinline__ void count_step_exact(double di, double li, double sigma, double &a,
+                                                 double &cp, int &sp, int &cnt) {
+    double c = fma(di, cp, a);
+    const bool z = is_zero(c);
+    const int sc = z ? (sp ^ 1) : sign_bit(c);
+    cnt += sc ^ sp;
+    a = fma(-sigma, c, li * a);
+    const int ex = biased_exp(c);
+    if ((unsigned)(ex - (1023 - 200)) > 400u && !z) {
+        const double s = pow2i(1023 - ex);
+        c *= s;
+        a *= s;
+    }
+    cp = c;
+    sp = sc;
+}
+
 __device__ __forceinline__ int negcount_ldl(int n, const double *__restrict__ d,
                                             const double *__restrict__ dll, double sigma) {
     double a = -sigma, cp = 1.0;
-    int sp = 0, cnt = 0;
+    int sp = 0, cnt = 0, i = 0;
     double dn = __ldg(d), ln = (n > 1) ? __ldg(dll) : 0.0; // prefetched data of step i
-    for (int i = 0; i < n - 1; ++i) {
+    for (; i + 8 < n; i += 8) {
+        const double a0 = a, c0 = cp;
+        const int sp0 = sp, cnt0 = cnt;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const double di = dn, li = ln;
+            dn = __ldg(d + i + u + 1);
+            ln = (i + u + 1 < n - 1) ? __ldg(dll + i + u + 1) : 0.0;
+            const double t = li * a;
+            const double c = fma(di, cp, a);
+            const int sc = sign_bit(c);
+            cnt += sc ^ sp;
+            sp = sc;
+            a = fma(-sigma, c, t);
+            cp = c;
+        }
+        const int ex = biased_exp(cp), ea = biased_exp(a);
+        if (__builtin_expect(ea == 0x7ff || (unsigned)(ex - 100) > 1800u, 0)) {
+            a = a0;
+            cp = c0;
+            sp = sp0;
+            cnt = cnt0;
+            for (int k = i; k < i + 8; ++k)
+                count_step_exact(__ldg(d + k), (k < n - 1) ? __ldg(dll + k) : 0.0, sigma, a, cp, sp, cnt);
+        }
+        const double q = norm_pow2(cp);
+        cp *= q;
+        a *= q;
+    }
+    for (; i < n - 1; ++i) {
         const double di = dn, li = ln;
         dn = __ldg(d + i + 1);
         ln = (i + 1 < n - 1) ? __ldg(dll + i + 1) : 0.0;
-        const double t = li * a;
-        double c = fma(di, cp, a);
-        const bool z = is_zero(c);
-        const int sc = z ? (sp ^ 1) : sign_bit(c);
-        cnt += sc ^ sp;
-        a = fma(-sigma, c, t);
-        const int ex = biased_exp(c);
-        if ((unsigned)(ex - (1023 - 200)) > 400u && !z) {
-            const double s = pow2i(1023 - ex);
-            c *= s;
-            a *= s;
-        }
-        cp = c;
-        sp = sc;
+        count_step_exact(di, li, sigma, a, cp, sp, cnt);
     }
-    double c = fma(dn, cp, a);
-    int sc = is_zero(c) ? (sp ^ 1) : sign_bit(c);
+    const double c = fma(dn, cp, a);
+    const int sc = is_zero(c) ? (sp ^ 1) : sign_bit(c);
     cnt += sc ^ sp;
     return cnt;
 }

@@ -544,49 +544,100 @@ void launch_refine_ends(int ncluster, const ClusterItem *clusters, const Node *n
 
 // Trial dstqds L+ D+ L+^T = L D L^T - tau I in homogeneous form (see negcount_ldl).
 // Existence: no exact zero pivot and finite values.  Element growth: max |d+_i|, the
-// division c_i / c_{i-1} being off the recurrence's critical path.  With store, the
+// division c_i / c_{i-1} being off the recurrence's critical path.  With STORE, the
 // unscaled c_i go to U[i] and the power-of-two rescale applied after step i to K[i].
+// As in negcount_ldl the loop runs in blocks of 8 steps without a data-dependent branch
+// and normalises (a, c) at the end of a block (K[i] is nonzero only there); a block that
+// met a zero pivot or left the safe range is redone with the per-step rules.
+
+// One step with the per-step rules.
+template <bool STORE>
+__device__ __forceinline__ void trial_step_exact(int i, bool last, double di, double li, double tau,
+                                                 double *U, int *K, int kstride, double &a,
+                                                 double &cp, bool &zero, double &gn, double &gd) {
+    double c = fma(di, cp, a);
+    const bool z = is_zero(c);
+    zero |= z;
+    c = z ? -cp * 0x1p-80 : c;
+    const double ac = fabs(c), acp = fabs(cp);
+    const bool up = ac * gd > gn * acp;
+    gn = up ? ac : gn;
+    gd = up ? acp : gd;
+    int k = 0;
+    if (!last) {
+        a = fma(-tau, c, li * a);
+        if (STORE) U[i] = c;
+        const int ex = biased_exp(c);
+        if ((unsigned)(ex - (1023 - 200)) > 400u) {
+            k = 1023 - ex;
+            const double sc = pow2i(k);
+            c *= sc;
+            a *= sc;
+        }
+    } else if (STORE) {
+        U[i] = c;
+    }
+    if (STORE) K[(size_t)i * kstride] = k;
+    cp = c;
+}
+
+template <bool STORE>
 __device__ void trial_shift(int n, const double *__restrict__ d, const double *__restrict__ dll,
-                            double tau, bool store, double *U, int *K, int kstride, bool &exists,
+                            double tau, double *U, int *K, int kstride, bool &exists,
                             double &growth) {
     double a = -tau, cp = 1.0;
     bool zero = false;
-    // running maximum of |c_i / c_{i-1}| kept as a fraction gn / gd: no division and no
-    // data-dependent branch on the recurrence's critical path (non-finite values propagate
-    // and are caught once at the end)
+    // running maximum of |c_i / c_{i-1}| kept as a fraction gn / gd: no division on the
+    // recurrence's critical path (non-finite values propagate and are caught at the end)
     double gn = 0.0, gd = 1.0;
     // operands of step i + 1 are loaded while step i runs (software prefetch)
     double dn = __ldg(d), ln = (n > 1) ? __ldg(dll) : 0.0;
-    for (int i = 0; i < n; ++i) {
+    int i = 0;
+    for (; i + 8 < n; i += 8) {
+        const double a0 = a, c0 = cp, gn0 = gn, gd0 = gd;
+        bool bad = false;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const double di = dn, li = ln;
+            dn = __ldg(d + i + u + 1);
+            ln = (i + u + 1 < n - 1) ? __ldg(dll + i + u + 1) : 0.0;
+            const double c = fma(di, cp, a);
+            bad |= is_zero(c);
+            const double ac = fabs(c), acp = fabs(cp);
+            const bool up = ac * gd > gn * acp;
+            gn = up ? ac : gn;
+            gd = up ? acp : gd;
+            a = fma(-tau, c, li * a);
+            if (STORE) {
+                U[i + u] = c;
+                K[(size_t)(i + u) * kstride] = 0;
+            }
+            cp = c;
+        }
+        const int ex = biased_exp(cp), ea = biased_exp(a);
+        if (__builtin_expect(bad || ea == 0x7ff || (unsigned)(ex - 100) > 1800u, 0)) {
+            a = a0;
+            cp = c0;
+            gn = gn0;
+            gd = gd0;
+            for (int k = i; k < i + 8; ++k)
+                trial_step_exact<STORE>(k, false, __ldg(d + k), __ldg(dll + k), tau, U, K, kstride,
+                                        a, cp, zero, gn, gd);
+        } else {
+            const int k = 1023 - ex;
+            const double q = pow2i(k);
+            cp *= q;
+            a *= q;
+            if (STORE) K[(size_t)(i + 7) * kstride] = k;
+        }
+    }
+    for (; i < n; ++i) {
         const double di = dn, li = ln;
         if (i + 1 < n) {
             dn = __ldg(d + i + 1);
             ln = (i + 1 < n - 1) ? __ldg(dll + i + 1) : 0.0;
         }
-        double c = fma(di, cp, a);
-        const bool z = is_zero(c);
-        zero |= z;
-        c = z ? -cp * 0x1p-80 : c;
-        const double ac = fabs(c), acp = fabs(cp);
-        const bool up = ac * gd > gn * acp;
-        gn = up ? ac : gn;
-        gd = up ? acp : gd;
-        int k = 0;
-        if (i < n - 1) {
-            a = fma(-tau, c, li * a);
-            if (store) U[i] = c;
-            const int ex = biased_exp(c);
-            if ((unsigned)(ex - (1023 - 200)) > 400u) {
-                k = 1023 - ex;
-                const double sc = pow2i(k);
-                c *= sc;
-                a *= sc;
-            }
-        } else if (store) {
-            U[i] = c;
-        }
-        if (store) K[(size_t)i * kstride] = k;
-        cp = c;
+        trial_step_exact<STORE>(i, i == n - 1, di, li, tau, U, K, kstride, a, cp, zero, gn, gd);
     }
     const double g = gn / gd;
     exists = is_finite(tau) && !zero && is_finite(g) && is_finite(cp) && is_finite(a);
@@ -618,7 +669,7 @@ __global__ void k_shift_trials(int ncluster, const ClusterItem *__restrict__ clu
         if (side == 0 && (fault_mask & MR3_FAULT_NAN_SHIFT)) tau = NAN;
         bool ex = false;
         double g = INFINITY;
-        trial_shift(n, pd, pd + 2 * n, tau, true, side ? cd + n : cd, (int *)(cd + 2 * n) + side, 2,
+        trial_shift<true>(n, pd, pd + 2 * n, tau, side ? cd + n : cd, (int *)(cd + 2 * n) + side, 2,
                     ex, g);
         tri[2 * ci + side] = make_double2(ex ? 1.0 : 0.0, g);
         steps = n;
@@ -706,7 +757,7 @@ __global__ void k_shift_ladder(int nslots, int max_tries, const ClusterItem *__r
         const double *pd = pool + P.rep;
         bool ex = false;
         double g = INFINITY;
-        trial_shift(n, pd, pd + 2 * n, tau, false, nullptr, nullptr, 0, ex, g);
+        trial_shift<false>(n, pd, pd + 2 * n, tau, nullptr, nullptr, 0, ex, g);
         lad[(long long)li * NL + j] = make_double2(ex ? 1.0 : 0.0, g);
         steps = n;
     }
@@ -779,7 +830,7 @@ __global__ void k_shift_recompute(int nslots, const ClusterItem *__restrict__ cl
         double *cd = childpool + cluster_rep[ci];
         bool ex;
         double g;
-        trial_shift(n, pd, pd + 2 * n, dec[ci].tau, true, cd, (int *)(cd + 2 * n), 2, ex, g);
+        trial_shift<true>(n, pd, pd + 2 * n, dec[ci].tau, cd, (int *)(cd + 2 * n), 2, ex, g);
         steps = n;
     }
     for (int o = 16; o > 0; o >>= 1) steps += __shfl_xor_sync(FULL_MASK, steps, o);
