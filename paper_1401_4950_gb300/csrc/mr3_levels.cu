@@ -547,8 +547,8 @@ void launch_refine_ends(int ncluster, const ClusterItem *clusters, const Node *n
 // division c_i / c_{i-1} being off the recurrence's critical path.  With STORE, the
 // unscaled c_i go to U[i] and the power-of-two rescale applied after step i to K[i].
 // As in negcount_ldl the loop runs in blocks of 8 steps without a data-dependent branch
-// and normalises (a, c) at the end of a block (K[i] is nonzero only there); a block that
-// met a zero pivot or left the safe range is redone with the per-step rules.
+// and normalises (a, c) at the end of a block (K[i] is nonzero only there); a block in
+// which some c was zero or left [2^-400, 2^400] is redone with the per-step rules.
 
 // One step with the per-step rules.
 template <bool STORE>
@@ -602,7 +602,8 @@ __device__ void trial_shift(int n, const double *__restrict__ d, const double *_
             dn = __ldg(d + i + u + 1);
             ln = (i + u + 1 < n - 1) ? __ldg(dll + i + u + 1) : 0.0;
             const double c = fma(di, cp, a);
-            bad |= is_zero(c);
+            // zero, or outside [2^-400, 2^400] (the growth test multiplies two values)
+            bad |= (unsigned)(biased_exp(c) - (1023 - 400)) > 800u;
             const double ac = fabs(c), acp = fabs(cp);
             const bool up = ac * gd > gn * acp;
             gn = up ? ac : gn;
@@ -615,7 +616,7 @@ __device__ void trial_shift(int n, const double *__restrict__ d, const double *_
             cp = c;
         }
         const int ex = biased_exp(cp), ea = biased_exp(a);
-        if (__builtin_expect(bad || ea == 0x7ff || (unsigned)(ex - 100) > 1800u, 0)) {
+        if (__builtin_expect(bad || ea == 0x7ff, 0)) {
             a = a0;
             cp = c0;
             gn = gn0;

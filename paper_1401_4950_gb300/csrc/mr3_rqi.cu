@@ -187,44 +187,111 @@ __global__ void __launch_bounds__(32) k_rqi(int nsingle, const SingleItem *__res
             double c_last = 1.0, cprev_last = 1.0;
             if (!done && k < 2) {
                 const bool bw = (k == 1);
-                // steps: forward indices 0..fend (the step at fend only stores unless c_{n-1}
-                // is needed), backward indices n-2 .. blow
-                const int nsteps = bw ? (n - 1 - blow) : (fend + 1);
+                // regular steps (compute, store, next Y): forward indices 0..nreg-1 (then the
+                // step at fend: c_{n-1} for a full factorization or r = n-1, else a store
+                // only), backward indices n-2 .. blow
+                const int nreg = bw ? (n - 1 - blow) : (need_last ? n - 1 : fend);
                 const double *P = bw ? dll : d;
                 const double *Qv = bw ? d : dll;
                 double X = 1.0, Y = bw ? (__ldg(d + n - 1) - lam) : -lam;
                 int Sx = 0, sp = 0, cnt = 0;
                 if (bw) S.E(n - 1).y = 0;
-                // data of step t + 1 is loaded while step t runs (software prefetch)
-                int i = bw ? (n - 2) : 0;
-                const int di = bw ? -1 : 1;
-                double pi = (nsteps > 0) ? __ldg(P + i) : 0.0;
-                double qi = (nsteps > 0 && i < n - 1) ? __ldg(Qv + i) : 0.0;
-                for (int t = 0; t < nsteps; ++t, i += di) {
-                    const int inext = i + di;
-                    const bool more = t + 1 < nsteps;
-                    const double pn = more ? __ldg(P + inext) : 0.0;
-                    const double qn = (more && inext < n - 1) ? __ldg(Qv + inext) : 0.0;
-                    if (!bw) { S.A(i) = Y; S.C(i) = X; S.E(i).x = Sx; }
-                    if (!bw && i == fend && !need_last) break;
+                const int di = bw ? -1 : 1, i0 = bw ? (n - 2) : 0;
+                // the lane's slots: forward (A, C, E.x) = (a_i, c_{i-1}, exponent) stored
+                // before the step, backward (H, Q, E.y) = (h_i, d_i f_{i+1}, exponent) after it
+                const int off1 = (bw ? 2 : 0) * kTeams, off2 = (bw ? 3 : 1) * kTeams;
+                const int eoff = bw ? 1 : 0;
+                auto store = [&](int i, double v1, double v2, int e) {
+                    double *row = S.base + (size_t)i * Scratch<kTeams>::kSPI;
+                    row[off1] = v1;
+                    row[off2] = v2;
+                    ((int *)(row + 4 * kTeams))[eoff] = e;
+                };
+                // one regular step with the per-step rules (zero-pivot substitute, rescale)
+                auto step_exact = [&](int i, double pi, double qi) {
+                    const double Yb = Y, Xb = X;
                     const double qY = qi * Y;
                     double Xn = fma(pi, X, Y);
                     // an exactly zero pivot becomes a negative one 2^-80 times the
                     // cancelled term |pi X| = |Y|: tiny relative to the data at any scale
                     if (is_zero(Xn)) Xn = is_zero(Y) ? -X * 0x1p-80 : copysign(fabs(Y) * 0x1p-80, -X);
                     const int sc = sign_bit(Xn);
-                    if (bw || full || i < r) cnt += sc ^ sp;
-                    if (!bw && i == n - 1) { c_last = Xn; cprev_last = X; break; }
+                    cnt += sc ^ sp;
                     Y = fma(-lam, Xn, qY);
-                    if (bw) { S.H(i) = Xn; S.Q(i) = qY; S.E(i).y = Sx; }
+                    store(i, bw ? Xn : Yb, bw ? qY : Xb, Sx);
                     Sx -= rescale2(Xn, Y);
                     X = Xn;
                     sp = sc;
-                    pi = pn;
-                    qi = qn;
+                };
+                // blocks of 8 steps without a data-dependent branch (see negcount_ldl): the
+                // per-step rescale is replaced by a normalisation at the end of the block;
+                // a block in which some h or c was zero or left [2^-400, 2^400] (a flag
+                // collected off the recurrence, so that products of two stored values, as
+                // in the twist search, stay finite) is redone with the per-step rules
+                int t = 0;
+                double pn = (nreg > 0) ? __ldg(P + i0) : 0.0;
+                double qn = (nreg > 0) ? __ldg(Qv + i0) : 0.0;
+                for (; t + 8 <= nreg; t += 8) {
+                    const double X0 = X, Y0 = Y;
+                    const int Sx0 = Sx, sp0 = sp, cnt0 = cnt;
+                    bool flag = false;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int i = i0 + di * (t + u);
+                        const double pi = pn, qi = qn;
+                        const int inext = (t + u + 1 < nreg) ? i + di : i;
+                        pn = __ldg(P + inext);
+                        qn = __ldg(Qv + inext);
+                        const double Yb = Y, Xb = X;
+                        const double qY = qi * Y;
+                        const double Xn = fma(pi, X, Y);
+                        flag |= (unsigned)(biased_exp(Xn) - (1023 - 400)) > 800u;
+                        const int sc = sign_bit(Xn);
+                        cnt += sc ^ sp;
+                        sp = sc;
+                        Y = fma(-lam, Xn, qY);
+                        store(i, bw ? Xn : Yb, bw ? qY : Xb, Sx);
+                        X = Xn;
+                    }
+                    const int ex = biased_exp(X), ey = biased_exp(Y);
+                    if (__builtin_expect(flag || ey == 0x7ff, 0)) {
+                        X = X0;
+                        Y = Y0;
+                        Sx = Sx0;
+                        sp = sp0;
+                        cnt = cnt0;
+                        for (int u = 0; u < 8; ++u) {
+                            const int i = i0 + di * (t + u);
+                            step_exact(i, __ldg(P + i), __ldg(Qv + i));
+                        }
+                    } else {
+                        const int kx = 1023 - ex;
+                        const double q = pow2i(kx);
+                        X *= q;
+                        Y *= q;
+                        Sx -= kx;
+                    }
+                }
+                for (; t < nreg; ++t) {
+                    const int i = i0 + di * t;
+                    step_exact(i, __ldg(P + i), __ldg(Qv + i));
+                }
+                if (!bw) {
+                    // the step at fend (= n-1 or r)
+                    S.A(fend) = Y;
+                    S.C(fend) = X;
+                    S.E(fend).x = Sx;
+                    if (need_last) {
+                        double Xn = fma(__ldg(d + n - 1), X, Y);
+                        if (is_zero(Xn)) Xn = is_zero(Y) ? -X * 0x1p-80 : copysign(fabs(Y) * 0x1p-80, -X);
+                        const int sc = sign_bit(Xn);
+                        if (full || n - 1 < r) cnt += sc ^ sp;
+                        c_last = Xn;
+                        cprev_last = X;
+                    }
                 }
                 if (bw) cntb = cnt; else cntf = cnt;
-                steps += (unsigned long long)nsteps;
+                steps += (unsigned long long)(bw ? nreg : fend + 1);
             }
             __syncwarp();
             cntf = __shfl_sync(FULL_MASK, cntf, tbase);
