@@ -234,38 +234,6 @@ __device__ __forceinline__ int negcount_ldl(int n, const double *__restrict__ d,
     return cnt;
 }
 
-// Same count at two shifts at once (independent chains interleaved for latency
-// hiding); returns both counts.
-__device__ __forceinline__ void negcount_ldl2(int n, const double *__restrict__ d,
-                                              const double *__restrict__ dll, double s0,
-                                              double s1, int &k0, int &k1) {
-    double a0 = -s0, c0 = 1.0, a1 = -s1, c1 = 1.0;
-    int p0 = 0, p1 = 0, n0 = 0, n1 = 0;
-    double dn = __ldg(d), ln = (n > 1) ? __ldg(dll) : 0.0; // prefetched data of step i
-    for (int i = 0; i < n - 1; ++i) {
-        const double di = dn, li = ln;
-        dn = __ldg(d + i + 1);
-        ln = (i + 1 < n - 1) ? __ldg(dll + i + 1) : 0.0;
-        const double t0 = li * a0, t1 = li * a1;
-        double x0 = fma(di, c0, a0), x1 = fma(di, c1, a1);
-        const bool z0 = is_zero(x0), z1 = is_zero(x1);
-        const int q0 = z0 ? (p0 ^ 1) : sign_bit(x0), q1 = z1 ? (p1 ^ 1) : sign_bit(x1);
-        n0 += q0 ^ p0;
-        n1 += q1 ^ p1;
-        a0 = fma(-s0, x0, t0);
-        a1 = fma(-s1, x1, t1);
-        const int e0 = biased_exp(x0), e1 = biased_exp(x1);
-        if ((unsigned)(e0 - (1023 - 200)) > 400u && !z0) { const double s = pow2i(1023 - e0); x0 *= s; a0 *= s; }
-        if ((unsigned)(e1 - (1023 - 200)) > 400u && !z1) { const double s = pow2i(1023 - e1); x1 *= s; a1 *= s; }
-        c0 = x0; c1 = x1; p0 = q0; p1 = q1;
-    }
-    double x0 = fma(dn, c0, a0), x1 = fma(dn, c1, a1);
-    n0 += (is_zero(x0) ? (p0 ^ 1) : sign_bit(x0)) ^ p0;
-    n1 += (is_zero(x1) ? (p1 ^ 1) : sign_bit(x1)) ^ p1;
-    k0 = n0;
-    k1 = n1;
-}
-
 // NegCount on T itself (App. B, Alg. NegCount on T) in single precision, used only to
 // locate the extremal eigenvalues roughly before the root shift is chosen (the FP64
 // factorization then verifies definiteness).  Homogeneous three-term form of the pivot
