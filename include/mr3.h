@@ -18,12 +18,14 @@
  *  - Each eigenvector has unit 2-norm and an entry of largest magnitude is positive
  *    (entries equal in magnitude in exact arithmetic are ordered by rounding).
  *  - The caller owns every array; the library never frees caller memory.  The
- *    library takes its internal workspace with stream-ordered allocation
- *    (cudaMallocAsync) on the given stream and returns it before the call ends.
+ *    library takes its internal workspace with stream-ordered allocation on the given
+ *    stream from a memory pool of its own (see mr3_release_memory) and returns it to
+ *    the pool before the call ends.
  *  - stream is a cudaStream_t passed as void* (NULL = the legacy default stream).
  *    All device work is enqueued on it.  The solver calls read a few counters back
- *    to the host and therefore synchronise with the stream before returning; the
- *    results are complete when the call returns.
+ *    to the host (through a small mapped pinned buffer per host thread, allocated on
+ *    first use, so that no copy engine is involved) and therefore synchronise with the
+ *    stream before returning; the results are complete when the call returns.
  *  - Return value: 0 on success; -i when argument i (1-based) is invalid; a
  *    positive MR3_S* status when the result was produced but a safeguard fired
  *    (see mr3_info.status_counts); MR3_EOOM / MR3_ECUDA on resource errors.
