@@ -12,7 +12,7 @@
  *                                    (Sec. 2.3.1, "Bisection and inverse iteration")
  *   - cyclic Jacobi on a small dense symmetric matrix (textbook brute force, n <= 64)
  *
- * Readings of the paper taken here (each also listed in the design notes):
+ * Readings of the paper taken here, where the printed algorithms are ambiguous or garbled:
  *   - Gershgorin: the first row's radius is |beta_1|; the printed algorithm writes
  *     beta_1 without the absolute value, which would be wrong for beta_1 < 0.
  *   - Bisection stop test: iterate while the width exceeds

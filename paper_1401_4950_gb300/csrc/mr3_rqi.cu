@@ -92,7 +92,8 @@ template <int TEAM> __device__ __forceinline__ void team_argmax_bits(long long &
 // homogeneous variables of the Sturm count (see negcount_ldl),
 //   forward  (dstqds):  c_i = d_i c_{i-1} + a_i,      a_{i+1} = dll_i a_i - lam c_i,
 //                       d+_i = c_i / c_{i-1},          s_i = a_i / c_{i-1};
-//   backward (dqds, read as in the design notes: omega-_{i+1} = p_{i+1} + dll_i):
+//   backward (Alg. dqds, App. B, whose printed assignment to u- stands for omega-:
+//             omega-_{i+1} = p_{i+1} + dll_i):
 //                       h_i = dll_i h_{i+1} + f_{i+1}, f_i = d_i f_{i+1} - lam h_i,
 //                       omega-_{i+1} = h_i / h_{i+1},  p_i = f_i / h_i,
 // from c_{-1} = 1, a_0 = -lam, h_{n-1} = 1, f_{n-1} = d_{n-1} - lam, so that
