@@ -25,6 +25,22 @@ __host__ __device__ __forceinline__ long long rep_size(int n) { return (long lon
 __host__ __device__ __forceinline__ long long rep_df_offset(int n) { return 3ll * n + (n & 1); }
 __host__ __device__ __forceinline__ long long rep_q_offset(int n) { return rep_df_offset(n) + 2ll * n; }
 
+// Classification threshold of the binary64 tree when the caller leaves gaptol at its
+// default (Sec. 3.2.3).  The loss of orthogonality the tree attains grows like
+// eps / gaptol (the thesis quotes O(n eps / gaptol) as the observed worst case of the
+// bound on orthogonality, Sec. 3.1.2): two eigenvalues that are classified as singletons
+// at a relative gap just above gaptol get vectors whose inner product is a few eps /
+// gaptol.  Measured on Wilkinson-type pairs, that is about 3.6 eps / relgap, which only
+// stays below 10 n eps while gaptol >= 0.36 / n.  So blocks of small order n_b use
+// gaptol = 2 / n_b, capped at 0.05 (gaptol must stay well below 1 for clusters to break,
+// Ch. 5), and larger blocks keep the customary 1e-3.
+__host__ __device__ __forceinline__ double auto_gaptol(int nb) {
+    const double g = 2.0 / (double)(nb > 1 ? nb : 1);
+    return g < 1e-3 ? 1e-3 : (g > 0.05 ? 0.05 : g);
+}
+// Sentinel passed as gaptol: choose auto_gaptol(n_b) per block.
+constexpr double kGaptolAuto = 0.0;
+
 // One input matrix of a (possibly batched) solve.
 struct MatDesc {
     long long off;  // first row in the packed d/e arrays

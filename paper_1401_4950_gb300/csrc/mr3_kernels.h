@@ -93,6 +93,23 @@ int rqi_team(long long nsingle, int nmat);
 int rqi_scratch_per_index(int team);
 int rqi_singles_per_slot(int team);
 
+// Forces the kernels of one translation unit to be loaded on the current device (the
+// runtime otherwise loads each kernel at its first launch, which can allocate device
+// memory); returns the first error.  Used by the set-up of mr3_stemr_static.
+template <class... K> cudaError_t load_kernels(K... k) {
+    cudaError_t err = cudaSuccess;
+    cudaFuncAttributes a;
+    const void *fns[] = {(const void *)k...};
+    for (const void *f : fns) {
+        const cudaError_t e = cudaFuncGetAttributes(&a, f);
+        if (e != cudaSuccess && err == cudaSuccess) err = e;
+    }
+    return err;
+}
+cudaError_t preload_prologue();
+cudaError_t preload_levels();
+cudaError_t preload_rqi();
+
 // ---- double-double representation tree (mr3_ddpath.cu, opts->prec = MR3_DD).  A pool
 // holding representations keeps the leading words in the binary64 layout and the low
 // words in a second plane at the same offsets (pool_lo).

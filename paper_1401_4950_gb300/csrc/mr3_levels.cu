@@ -285,7 +285,8 @@ void launch_grid(int nblk, const BlkDesc *blks, const Node *nodes, const double 
 
 // One warp per node.  Consecutive eigenvalues j, j+1 of the node are separated when
 //   reldist(j, j+1) = (lo_{j+1} - hi_j) / max(|lo_j|, |hi_j|, |lo_{j+1}|, |hi_{j+1}|) >= gaptol
-// (Sec. 3.2.3, Classification).  The boundary flags of 32 columns at a time are combined
+// (Sec. 3.2.3, Classification); gaptol == kGaptolAuto selects auto_gaptol(n_b) for the
+// node's block.  The boundary flags of 32 columns at a time are combined
 // with a ballot; groups of one column become singletons, longer groups clusters.  Items
 // are appended with one atomic per warp and kind.  gapl/gapr receive the absolute gaps
 // of every column to its neighbours (used by the RQI acceptance test).
@@ -300,6 +301,7 @@ __global__ void k_classify(int nnode, const Node *__restrict__ nodes, const BlkD
     const Node N = nodes[w];
     if (N.c1 < N.c0) return;
     const int nb = blks[N.blk].n;
+    const double gt = (gaptol == kGaptolAuto) ? auto_gaptol(nb) : gaptol;
     int gstart = N.c0;
     int maxsize = 0, nclus = 0;
     for (int base = N.c0; base <= N.c1; base += 32) {
@@ -315,7 +317,7 @@ __global__ void k_classify(int nnode, const Node *__restrict__ nodes, const BlkD
                 hn = hi[c + 1];
                 const double den = fmax(fmax(fabs(l), fabs(h)), fmax(fabs(ln), fabs(hn)));
                 const double rd = (ln - h) / den;
-                end = !(rd < gaptol); // also separates on NaN (never join on bad data)
+                end = !(rd < gt); // also separates on NaN (never join on bad data)
             } else {
                 end = true;
             }
@@ -1070,6 +1072,13 @@ void launch_sort_outputs(int mi, int m, const MatDesc *mats, double *w, double *
     k_rank<<<(m + 255) / 256, 256, 0, s>>>(mats, mi, w, perm, wtmp);
     k_gather_cols<<<(m + 7) / 8, 256, 0, s>>>(mats, mi, perm, Z, ztmp);
     k_copy_back<<<(m + 7) / 8, 256, 0, s>>>(mats, mi, wtmp, ztmp, w, Z);
+}
+
+cudaError_t preload_levels() {
+    return load_kernels(k_bisect2, k_grid_counts, k_grid_bracket, k_classify, k_refine_ends,
+                        k_shift_trials, k_shift_select, k_shift_ladder, k_shift_pick,
+                        k_shift_recompute, k_shift, k_order_fix, k_rank, k_gather_cols,
+                        k_copy_back);
 }
 
 } // namespace mr3

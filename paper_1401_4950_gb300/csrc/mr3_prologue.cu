@@ -689,4 +689,11 @@ void launch_zero_z(int nmat, const MatDesc *mats, double *Z, cudaStream_t s) {
     }
 }
 
+cudaError_t preload_prologue() {
+    return load_kernels(k_mat_norm, k_split_flags, k_scan_tiles, k_scan_sums, k_scan_add,
+                        k_blocks_from_flags, k_blocks_finish, k_mat_blockcount, k_blk_setup,
+                        k_index_multi, k_assign_columns, k_root, k_init_columns, k_outer_gaps,
+                        k_zero_z);
+}
+
 } // namespace mr3

@@ -499,4 +499,6 @@ int rqi_team(long long nsingle, int nmat) {
 int rqi_scratch_per_index(int team) { return kScratchPerSingleton * (32 / team); }
 int rqi_singles_per_slot(int team) { return 32 / team; }
 
+cudaError_t preload_rqi() { return load_kernels(k_rqi<2>, k_rqi<8>); }
+
 } // namespace mr3

@@ -11,10 +11,15 @@
 // allowed to enter an allocator at all.  Such callers get a solver with a fixed footprint
 // here: the array below, reserved when this translation unit's module is loaded.
 //
-// Set-up: on the first call made with a given device current, the address of that
-// device's copy of the array is looked up once (cudaGetSymbolAddress) and cached; later
-// calls reuse it.  That lookup can load the module, so the first call on each device
-// should come before the caller begins any stream capture.
+// Set-up: on the first call made with a given device current (any order n up to the
+// limit, n = 0 included), the library loads, on that device, every kernel this entry point
+// launches and the array itself, and looks up the address of that device's copy of the
+// array once (cudaGetSymbolAddress) and caches it; later calls reuse it.  The runtime
+// otherwise loads each kernel at its first launch, and loading takes device memory.  So a
+// caller that claims its device memory up front should make one call per device (n = 0
+// is enough) before doing so, and the first call on each device should come before the
+// caller begins any stream capture.  None of these kernels uses a stack frame, so no
+// launch grows the device's local-memory reservation.
 //
 // Sharing: each device has exactly one array.  Two calls that overlap in time on the same
 // device (two host threads, or two streams not ordered with respect to each other) write
@@ -45,7 +50,9 @@ int static_scratch(void **out) {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_scratch_addr[dev]) {
         void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p ||
+            preload_prologue() != cudaSuccess || preload_levels() != cudaSuccess ||
+            preload_rqi() != cudaSuccess) {
             cudaGetLastError();
             return MR3_ECUDA;
         }
@@ -117,7 +124,7 @@ int lanes_auto(long long nactive, int tpe) {
 // The solve of one matrix (M filled in by the entry point) on the array behind `ar`.
 int solve_static(MatDesc &M, const double *d, const double *e, int range, double *w, double *Z,
                  const mr3_opts *opts, mr3_info &out, Arena &ar, cudaStream_t s) {
-    const double gaptol = (opts && opts->gaptol > 0.0) ? opts->gaptol : 1e-3;
+    const double gaptol = (opts && opts->gaptol > 0.0) ? opts->gaptol : kGaptolAuto;
     const unsigned long long seed = (opts && opts->seed) ? opts->seed : 0x5EEDull;
     const int max_rqi = (opts && opts->max_rqi > 0) ? opts->max_rqi : 10;
     const int max_tries = (opts && opts->max_shift_tries > 0) ? opts->max_shift_tries : 8;
@@ -191,7 +198,7 @@ int solve_static(MatDesc &M, const double *d, const double *e, int range, double
     SCK(cudaMemsetAsync(cnode, 0xff, sizeof(int) * ncols, s));
     launch_root(nblk, blks, d, e, pool0, f32, seed, s);
     launch_init_columns(nblk, blks, nodes0, cnode, jloc, lo, hi, (int)ncols, s);
-    const double rtol = 1e-2 * gaptol;
+    const double rtol = 1e-2 * (gaptol > 0.0 ? gaptol : 1e-3);
     if (range != MR3_RANGE_ALL) launch_outer_gaps(nblk, blks, nodes0, pool0, rtol, dinfo, s);
     if (M.nblk > 1) launch_zero_z(1, dmats, Z, s);
     launch_grid(nblk, blks, nodes0, pool0, grid, lo, hi, M.m, dinfo, s);
@@ -323,15 +330,15 @@ extern "C" int mr3_stemr_static(int n, const double *d, const double *e, int ran
         if (info) *info = out;
         return MR3_ENOSCRATCH;
     }
-    if (n == 0) {
-        if (info) *info = out;
-        return 0;
-    }
     void *base = nullptr;
-    const int src = static_scratch(&base);
+    const int src = static_scratch(&base); // set-up on the first call per device
     if (src) {
         if (info) *info = out;
         return src;
+    }
+    if (n == 0) {
+        if (info) *info = out;
+        return 0;
     }
     MatDesc M;
     std::memset(&M, 0, sizeof(M));
