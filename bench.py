@@ -1,12 +1,18 @@
 #!/usr/bin/env python3
-"""Benchmark of the GB300 MRRR path: eigenpairs/s for all eigenpairs of n = 8192 FP64
-symmetric tridiagonals (one 1-2-1, one Wilkinson W+ and one uniform(-1,1) matrix per
-step, solved together by one mr3_stemr_batched call; --solver single times one mr3_stemr
-call per matrix), with a live roofline of the dominant kernel, the CPU oracle timed
-beside it, an end-to-end number (pinned host buffers copied in and out inside the timed
-region), and SM clocks sampled during the timed region.
+"""Benchmark of the GB300 MRRR path.
+
+The headline line times all eigenpairs of n = 8192 FP64 symmetric tridiagonals (one
+1-2-1, one Wilkinson W+ and one uniform(-1,1) matrix per step, solved together by one
+mr3_stemr_batched call; --solver single times one mr3_stemr call per matrix), with the
+accuracy of each matrix's result, a live roofline of the dominant kernel group, the CPU
+oracle timed beside it, an end-to-end number through mr3_stemr_batched_host (host buffers
+copied in and out inside the timed call), and SM clocks sampled during the timed region.
+The same line carries the other parts of the metric: batched solves/s (4096 matrices of
+orders 32..1024, one call against per-matrix calls), backward / forward time at n = 4096,
+and the n = 20000 glued Wilkinson subset with the binary64 and the double-double tree.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mr3|reference] [--config c2]
+                  [--no-extras]
 
 Under torchrun (N > 1) every rank solves its own copy of the step's matrices (the
 problems are independent: weak scaling, no collective on the data path); the time is
@@ -36,6 +42,19 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 pipe of a GB300: 152 SMs x 2 DFMA/clk (measured: 1.19 TFLOP/s at 1995 MHz) x 2 flop
 # x 2070 MHz maximum SM clock.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+# A binary64 division occupies the FP64 pipe for about 10 DFMA issue slots (measured with
+# dependent a/b chains against FMA chains): in the divide-weighted count a division is
+# 20 flop-equivalents at the pipe's peak instead of 1 flop.
+DIV_FLOP_EQ = 20.0
+# Oracle sample of both CPU legs (the cpu_baseline of the headline line and the
+# reference arm): consecutive mid-spectrum eigenpairs per matrix.
+ORACLE_SAMPLE = 256
+# DRAM traffic per launch of the dominant kernel group, from an ncu capture of the same
+# workload (dram__bytes_read.sum + dram__bytes_write.sum, summed over the group's launches
+# of one step and divided by their number), valid only while the kernel source it was
+# taken on is unchanged: source file, its sha256 prefix at capture time, and the summary
+# under profiles/ that holds the counters.
+TRAFFIC = {}
 
 CONFIGS = {
     "c1": {"workload": "plain MRRR, n=1000 uniform(-1,1) d and e, all eigenpairs, FP64",
@@ -120,6 +139,20 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ CPU oracle legs
 
+def host_info():
+    """The host the CPU legs ran on: logical CPUs and the CPU model."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
 def oracle_sample(mats, per_matrix):
     """Oracle eigenpairs for `per_matrix` consecutive indices from the middle of each
     matrix's spectrum; returns (eigenpairs, seconds)."""
@@ -136,34 +169,32 @@ def oracle_sample(mats, per_matrix):
     return count, time.perf_counter() - t0
 
 
-def calibrate_sample(mats, budget_s):
-    per = 16
-    while True:
-        cnt, dt = oracle_sample(mats, per)
-        if dt * 2.2 > budget_s or per >= 4096:
-            return per, cnt, dt
-        per *= 2
+def _sample_text(per, nmat):
+    return ("%d consecutive mid-spectrum eigenpairs of each of the %d matrices (bisection to "
+            "full accuracy + inverse iteration with MGS), single thread" % (per, nmat))
 
 
-def cpu_baseline(mats, budget_s=15.0):
-    per, cnt, dt = calibrate_sample(mats, budget_s)
-    return {"value": cnt / dt, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle",
-            "sample": "%d consecutive mid-spectrum eigenpairs of each of the %d matrices "
-                      "(bisection to full accuracy + inverse iteration with MGS), %.1f s, "
-                      "single thread" % (per, len(mats), dt)}
+def cpu_baseline(mats, reps=2):
+    """The oracle on the same sample as the reference arm, timed `reps` times (~10 s)."""
+    cnt, tot = 0, 0.0
+    for _ in range(reps):
+        c, t = oracle_sample(mats, ORACLE_SAMPLE)
+        cnt += c
+        tot += t
+    return {"value": cnt / tot, "unit": "eigenpairs/s", "cores": 1, "kind": "oracle",
+            "sample": _sample_text(ORACLE_SAMPLE, len(mats)) + ", %d repetitions, %.1f s" % (reps, tot),
+            "host": host_info()}
 
 
 def run_reference(args, cfg, rank):
     if rank != 0:
         return
     mats = _matrices(cfg, args.n)
-    budget = max(2.0, 150.0 / (args.steps + args.warmup))
-    per, _, _ = calibrate_sample(mats, budget)
     for _ in range(args.warmup):
-        oracle_sample(mats, per)
+        oracle_sample(mats, ORACLE_SAMPLE)
     tot_cnt, tot_t = 0, 0.0
     for _ in range(args.steps):
-        c, t = oracle_sample(mats, per)
+        c, t = oracle_sample(mats, ORACLE_SAMPLE)
         tot_cnt += c
         tot_t += t
     value = tot_cnt / tot_t
@@ -172,10 +203,10 @@ def run_reference(args, cfg, rank):
             "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": _workload(cfg, args.n),
-                                            "sample_per_matrix": per},
+                                            "sample_per_matrix": ORACLE_SAMPLE},
             "cpu_baseline": {"value": value, "unit": "eigenpairs/s", "cores": 1,
-                             "kind": "oracle",
-                             "sample": "%d mid-spectrum eigenpairs per matrix per step" % per},
+                             "kind": "oracle", "sample": _sample_text(ORACLE_SAMPLE, len(mats)),
+                             "host": host_info()},
             "e2e": {"value": value, "unit": "eigenpairs/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -200,7 +231,39 @@ def job_value(units_per_rank, world, ms_per_step):
     return world * units_per_rank / (ms_per_step / 1e3)
 
 
-# ------------------------------------------------------------------ GPU leg
+# ------------------------------------------------------------------ accuracy on the device
+
+def gpu_gates(d, e, w, Z, tnorm):
+    """Scaled residual max ||T z - lambda z|| / (n eps ||T||) and orthogonality
+    max |Z^T Z - I| / (n eps), computed with plain torch operations on the device."""
+    import torch
+    n = d.shape[0]
+    TZ = d[:, None] * Z
+    TZ[:-1] += e[:n - 1, None] * Z[1:]
+    TZ[1:] += e[:n - 1, None] * Z[:-1]
+    R = TZ - Z * w[None, :]
+    resid = torch.linalg.vector_norm(R, dim=0).max().item() / (n * EPS * tnorm)
+    G = Z.T @ Z
+    G.diagonal().sub_(1.0)
+    orth = G.abs().max().item() / (n * EPS)
+    return resid, orth
+
+
+def _source_sha(path):
+    import hashlib
+    return hashlib.sha256(open(os.path.join(ROOT, path), "rb").read()).hexdigest()[:16]
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch of `kernel` from its capture, or None when the kernel's source
+    changed after the capture (or no capture exists)."""
+    t = TRAFFIC.get(kernel)
+    if not t or _source_sha(t["source"]) != t["sha"]:
+        return None
+    return t["bytes_per_launch"]
+
+
+# ------------------------------------------------------------------ GPU legs
 
 def run_gpu(args, cfg, rank, world):
     import torch
@@ -228,14 +291,20 @@ def run_gpu(args, cfg, rank, world):
     dcat, ecat = torch.tensor(dcat_h, device=dev), torch.tensor(ecat_h, device=dev)
 
     def step():
+        """One step; returns the solver statistics and each matrix's (w, Z) on the device."""
         if args.solver == "single":
-            infos = []
+            infos, res = [], []
             for _, d, e in dev_mats:
-                _, _, info = mr3.stemr(d, e, opts=opts)
+                w, Z, info = mr3.stemr(d, e, opts=opts)
                 infos.append(info)
-            return infos
-        _, _, _, _, info = mr3.stemr_batched(n_off, dcat, ecat, opts=opts)
-        return [info]
+                res.append((w, Z))
+            return infos, res
+        _, w, Z, z_off, info = mr3.stemr_batched(n_off, dcat, ecat, opts=opts)
+        res = []
+        for b, n in enumerate(sizes):
+            res.append((w[n_off[b]:n_off[b] + n],
+                        Z[z_off[b]:z_off[b] + n * n].view(n, n).t()))
+        return [info], res
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -246,7 +315,7 @@ def run_gpu(args, cfg, rank, world):
           for _ in range(args.steps)]
     agg = {"kernel_ms": np.zeros(8), "kernel_launches": np.zeros(8, dtype=np.int64),
            "sturm_steps": 0, "shift_steps": 0, "twisted_steps": 0}
-    last_infos = None
+    last = None
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
@@ -254,14 +323,14 @@ def run_gpu(args, cfg, rank, world):
     for k in range(args.steps):
         flush.fill_(float(k))  # L2 (129 MB) flushed between timed steps
         ev[k][0].record(stream)
-        infos = step()
+        infos, res = step()
         ev[k][1].record(stream)
         for inf in infos:
             agg["kernel_ms"] += np.array(inf["kernel_ms"])
             agg["kernel_launches"] += np.array(inf["kernel_launches"])
             for key in ("sturm_steps", "shift_steps", "twisted_steps"):
                 agg[key] += inf[key]
-        last_infos = infos
+        last = (infos, res)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
@@ -272,105 +341,92 @@ def run_gpu(args, cfg, rank, world):
     ms_per_step = tot_ms / args.steps
     value = job_value(units_per_step, world, ms_per_step)
 
+    # ---- accuracy of the last timed step's results (outside the timed region): the
+    # spec gates, residual and orthogonality scaled by n eps ||T|| and n eps
+    accuracy = []
+    for (kind, d, e), (w, Z) in zip(dev_mats, last[1]):
+        tn = max(abs(w[0].item()), abs(w[-1].item()))
+        r, o = gpu_gates(d, e, w, Z, tn)
+        accuracy.append({"matrix": kind, "n": int(d.shape[0]), "resid": round(r, 4),
+                         "orth": round(o, 4)})
+    del last
+
     # ---- dominant kernel group and its roofline (FP64 pipe).  Algorithmic work per unit
     # (App. B recurrences): a Sturm-count step 5 flops (add, divide, multiply, FMA), a
-    # dstqds trial step 5, a twisted-factorization step 5.5; the units are the steps the
-    # library counts on the device, the time the group's CUDA events on its stream.
+    # dstqds trial step 5, a twisted-factorization step 5.5, each with one division; the
+    # units are the steps the library counts on the device, the time the group's CUDA
+    # events on its stream.  The divide-weighted count charges each division at its
+    # measured cost on the pipe (DIV_FLOP_EQ flop-equivalents).
     g = agg["kernel_ms"]
     kl = agg["kernel_launches"]
     groups = {"k_bisect2 (root and child refinement)":
-                  (g[2] + g[6], kl[2] + kl[6], agg["sturm_steps"], "Sturm step", 5.0),
-              "k_rqi": (g[4], kl[4], agg["twisted_steps"], "twisted-factorization step", 5.5),
+                  (g[2] + g[6], kl[2] + kl[6], agg["sturm_steps"], "Sturm step", 5.0, "k_bisect2"),
+              "k_rqi": (g[4], kl[4], agg["twisted_steps"], "twisted-factorization step", 5.5,
+                        "k_rqi"),
               "k_refine_ends + k_shift_*": (g[5], kl[5], agg["shift_steps"],
-                                            "cluster-end Sturm / dstqds step", 5.0)}
+                                            "cluster-end Sturm / dstqds step", 5.0, "k_shift")}
     dom = max(groups, key=lambda k: groups[k][0])
-    ms, launches, units, unit_name, fpu = groups[dom]
+    ms, launches, units, unit_name, fpu, kname = groups[dom]
+    fpu_w = fpu - 1.0 + DIV_FLOP_EQ
     achieved = (fpu * units / 1e12) / (ms / 1e3) if ms > 0 else 0.0
+    achieved_w = (fpu_w * units / 1e12) / (ms / 1e3) if ms > 0 else 0.0
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "FP64 pipe: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (no FP64 "
-                               "figure in the measured peaks)",
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": traffic_for(kname),
+                "frac_divide_weighted": achieved_w / FP64_PEAK_TFLOPS,
+                "peak_source": "FP64 pipe: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz, from unit "
+                               "counts and the maximum clock (MEASURED_PEAKS.json has no FP64 "
+                               "figure; a microbenchmark measured 1.19 TFLOP/s at 1995 MHz)",
                 "algorithmic": {"unit": unit_name, "flops_per_unit": fpu,
+                                "flops_per_unit_divide_weighted": fpu_w,
                                 "units_per_launch": units / max(launches, 1),
-                                "ms_per_launch": ms / max(launches, 1)},
+                                "ms_per_launch": ms / max(launches, 1),
+                                "z_bytes_per_step": int(8 * sum(n * n + n for n in sizes))},
                 "kernel_share": float(ms / max(g.sum(), 1e-9))}
+    if TRAFFIC.get(kname):
+        roofline["traffic_source"] = {k: TRAFFIC[kname][k] for k in ("profile", "sha", "source")}
 
-    # ---- end to end through the public API: every step copies its inputs from pinned host
-    # memory to the device, solves, and reads w and Z back into pinned host memory
-    import ctypes
-    L = mr3.lib()
-    nmax = max(sizes)
-    if args.solver == "single":
-        Zh = torch.empty((nmax, nmax), dtype=torch.float64, pin_memory=True).numpy()
-        wh = torch.empty(nmax, dtype=torch.float64, pin_memory=True).numpy()
-        hbuf = []
-        for _, d, e in mats:
-            dh = torch.empty(len(d), dtype=torch.float64, pin_memory=True).numpy()
-            eh = torch.empty(max(len(e), 1), dtype=torch.float64, pin_memory=True).numpy()
-            dh[:] = d
-            eh[: len(e)] = e
-            hbuf.append((dh, eh))
+    # ---- end to end through the C ABI on host buffers: every step is one
+    # mr3_stemr_batched_host call, which copies d and e in from pinned host memory, solves,
+    # and copies w and Z back into pinned host memory before returning
+    dh = torch.tensor(dcat_h).pin_memory()
+    eh = torch.tensor(ecat_h).pin_memory()
+    zlen = int(sum(n * n for n in sizes))
+    wh = torch.empty(int(n_off[-1]), dtype=torch.float64).pin_memory()
+    Zh = torch.empty(zlen, dtype=torch.float64).pin_memory()
+    e2e_opts = mr3.make_opts(prec=opts.prec)
 
-        def e2e_step():
-            for dh, eh in hbuf:
-                n = len(dh)
-                m = ctypes.c_int(0)
-                rc = L.mr3_stemr_host(n, dh.ctypes.data_as(ctypes.c_void_p),
-                                      eh.ctypes.data_as(ctypes.c_void_p), 0, 0.0, 0.0, 1, n,
-                                      ctypes.byref(m), wh.ctypes.data_as(ctypes.c_void_p),
-                                      Zh.ctypes.data_as(ctypes.c_void_p), n, ctypes.byref(opts),
-                                      None, ctypes.c_void_p(stream.cuda_stream))
-                assert rc in (0, 1, 2), rc
-    else:
-        # A serving loop: every step copies its inputs in from pinned host memory, solves,
-        # and reads w and Z back into one of two pinned host buffers on a copy stream,
-        # where the read of step k overlaps the solve of step k + 1 (the D2H of Z, 1.6 GB,
-        # takes 8 ms at the C2C link's 193 GB/s but was seen at ~16 GB/s on a box whose host
-        # was compacting memory).  The timed region ends when the last read is complete.
-        dh = torch.tensor(dcat_h).pin_memory()
-        eh = torch.tensor(ecat_h).pin_memory()
-        zlen = int(sum(n * n for n in sizes))
-        wh = [torch.empty(int(n_off[-1]), dtype=torch.float64, pin_memory=True) for _ in range(2)]
-        Zh = [torch.empty(zlen, dtype=torch.float64, pin_memory=True) for _ in range(2)]
-        dd_, ed_ = torch.empty_like(dcat), torch.empty_like(ecat)
-        copy_stream = torch.cuda.Stream(device=dev)
-        e2e_k = [0]
+    def e2e_step():
+        if args.solver == "single":
+            for _, d, e in mats:
+                mr3.stemr_host(d, e, opts=e2e_opts)
+        else:
+            mr3.stemr_batched_host(n_off, dh, eh, opts=e2e_opts, out=(wh, Zh))
 
-        def e2e_step():
-            slot = e2e_k[0] & 1
-            e2e_k[0] += 1
-            dd_.copy_(dh, non_blocking=True)
-            ed_.copy_(eh, non_blocking=True)
-            _, w, Z, _, _ = mr3.stemr_batched(n_off, dd_, ed_, opts=opts)
-            solved = torch.cuda.Event()
-            solved.record()
-            copy_stream.wait_event(solved)
-            with torch.cuda.stream(copy_stream):
-                wh[slot].copy_(w[: wh[slot].numel()], non_blocking=True)
-                Zh[slot].copy_(Z[:zlen], non_blocking=True)
-            # the outputs stay allocated until the copy stream has read them; a pinned slot
-            # is rewritten two steps later, after its previous read in copy-stream order
-            w.record_stream(copy_stream)
-            Z.record_stream(copy_stream)
     e2e_step()
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
     ne = max(2, min(args.steps, 5))
+    t0 = time.perf_counter()
     for _ in range(ne):
         e2e_step()
-    torch.cuda.synchronize()  # every step's read included
+    torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / ne
-    h2d = sum(8 * (len(d) + len(e)) for _, d, e in mats)
-    d2h = sum(8 * (len(d) + len(d) * len(d)) for _, d, _ in mats)
+    h2d = 8 * (len(dcat_h) + len(ecat_h))
+    d2h = 8 * (int(n_off[-1]) + zlen)
     e2e = {"value": world * units_per_step / e2e_s, "unit": "eigenpairs/s",
-           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-           "steps": ne, "d2h": "copy stream, overlapping the next step's solve"
-                              if args.solver != "single" else "inside mr3_stemr_host"}
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": ne,
+           "api": "mr3_stemr_batched_host (C ABI, pinned host buffers, copies inside the call)"
+                  if args.solver != "single" else "mr3_stemr_host per matrix (C ABI)"}
+    del dh, eh, wh, Zh
 
+    extras = {}
+    if not args.no_extras and world == 1:
+        extras["batched"] = batched_leg(args)
+        extras["backward"] = backward_leg(args)
+        extras["subset"] = subset_leg(args)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(mats, budget_s=args.cpu_budget)
-    info0 = last_infos[0] if last_infos else {}
+        cpu = cpu_baseline(mats)
     line = {"metric": "eigenpairs/s (n=8192 all, FP64)", "value": value, "unit": "eigenpairs/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -382,6 +438,7 @@ def run_gpu(args, cfg, rank, world):
                        "parallelism": "replicas, one set of matrices per GPU",
                        "solver": args.solver,
                        "tree": "double-double (Ch. 5)" if args.prec == "dd" else "binary64"},
+            "accuracy": accuracy,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(agg["kernel_launches"].sum()),
             "clocks": clk, "wall_s": wall,
@@ -392,21 +449,27 @@ def run_gpu(args, cfg, rank, world):
                 "rqi_iters_max", "bisect_fallbacks", "sturm_steps", "shift_steps",
                 "twisted_steps", "status")},
                 kernel_ms=[round(x, 3) for x in inf["kernel_ms"]])
-                for inf in (last_infos or [])],
+                for inf in infos],
             "step_ms": [round(x, 3) for x in step_ms]}
+    line.update(extras)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
 
-def run_batched(args):
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def batched_leg(args):
     """Batched workload: 4096 uniform(-1,1) tridiagonals with n_b uniform in [32, 1024], all
-    eigenpairs, one mr3_stemr_batched call vs one mr3_stemr call per matrix (same stream,
-    same accuracy).  Prints one JSON line (solves/s of both and their ratio)."""
+    eigenpairs, one mr3_stemr_batched call against one mr3_stemr call per matrix on the same
+    stream (same kernels, same accuracy); median of the timed calls."""
     import torch
     import paper_1401_4950_gb300 as mr3
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", torch.cuda.current_device())
     nb = args.batch
     sizes, n_off, d, e = tm.batched_random(nb)
     dt = torch.tensor(d, device=dev)
@@ -415,36 +478,44 @@ def run_batched(args):
     for _ in range(2):
         mr3.stemr_batched(n_off, dt, et, opts=opts)
     torch.cuda.synchronize()
-    reps = max(1, args.steps)
-    t0 = time.perf_counter()
+    reps = max(3, min(args.steps, 5))
+    tb = []
     for _ in range(reps):
+        a, b = _events()
+        a.record()
         m, w, Z, z_off, info = mr3.stemr_batched(n_off, dt, et, opts=opts)
-    torch.cuda.synchronize()
-    tb = (time.perf_counter() - t0) / reps
-    # per-matrix plain launches on the same data
+        b.record()
+        torch.cuda.synchronize()
+        tb.append(a.elapsed_time(b))
+        del w, Z
     views = [(dt[n_off[b]:n_off[b + 1]], et[n_off[b]:n_off[b + 1]]) for b in range(nb)]
     for b in range(min(nb, 8)):
         mr3.stemr(*views[b])
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    a, b_ = _events()
+    a.record()
     for b in range(nb):
         mr3.stemr(*views[b])
+    b_.record()
     torch.cuda.synchronize()
-    tp = time.perf_counter() - t0
-    line = {"metric": "batched solves/s (4096 tridiagonals, n in [32,1024], all eigenpairs, FP64)",
-            "value": nb / tb, "unit": "solves/s", "per_matrix_value": nb / tp,
-            "batched_over_per_matrix": tp / tb, "batched_ms": 1e3 * tb, "per_matrix_ms": 1e3 * tp,
-            "eigenpairs": int(n_off[-1]), "kernel_ms": [round(x, 3) for x in info["kernel_ms"]],
-            "dmax": info["dmax"], "nclusters": info["nclusters"], "rqi_iters": info["rqi_iters"]}
-    print(json.dumps(line), flush=True)
+    tp = a.elapsed_time(b_)
+    tbm = statistics.median(tb)
+    return {"metric": "batched solves/s (4096 tridiagonals, n in [32,1024], all eigenpairs, FP64)",
+            "value": nb / (tbm / 1e3), "unit": "solves/s", "per_matrix_value": nb / (tp / 1e3),
+            "batched_over_per_matrix": tp / tbm, "batched_ms": tbm, "batched_ms_all": tb,
+            "per_matrix_ms": tp, "eigenpairs": int(n_off[-1]),
+            "kernel_ms": [round(x, 3) for x in info["kernel_ms"]], "dmax": info["dmax"],
+            "nclusters": info["nclusters"], "rqi_iters": info["rqi_iters"],
+            "config": "sizes seed 401; matrix b: d seed 402+2b, e seed 403+2b"}
 
 
-def run_backward(args):
-    """Backward vs forward at n = 4096 (uniform(-1,1) d and e, all eigenpairs): loss
-    sum(g . lambda) + sum(G o Z), g and G standard normal.  Prints one JSON line."""
+def backward_leg(args):
+    """Backward vs forward at n = 4096 (uniform(-1,1) d and e seeds 501, 502, all
+    eigenpairs): loss sum(g . lambda) + sum(G o Z), g and G standard normal (seeds 503,
+    504); median device times of mr3_stemr and of mr3_backward."""
     import torch
     import paper_1401_4950_gb300 as mr3
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", torch.cuda.current_device())
     n = args.n_bwd
     d, e = tm.random_uniform(n, 501, 502)
     g = torch.tensor(tm.normal(503, n), device=dev)
@@ -454,44 +525,34 @@ def run_backward(args):
         w, Z, _ = mr3.stemr(dt, et)
         mr3.backward(w, Z, g, G)
     torch.cuda.synchronize()
-    reps = max(1, args.steps)
-    t0 = time.perf_counter()
+    reps = max(5, min(args.steps, 10))
+    tf, tb = [], []
     for _ in range(reps):
+        a, b = _events()
+        a.record()
         w, Z, _ = mr3.stemr(dt, et)
-    torch.cuda.synchronize()
-    tf = (time.perf_counter() - t0) / reps
-    t0 = time.perf_counter()
-    for _ in range(reps):
-        dd, de = mr3.backward(w, Z, g, G)
-    torch.cuda.synchronize()
-    tb = (time.perf_counter() - t0) / reps
-    print(json.dumps({"metric": "backward / forward time (n=%d, all eigenpairs, FP64)" % n,
-                      "value": tb / tf, "unit": "ratio", "forward_ms": 1e3 * tf,
-                      "backward_ms": 1e3 * tb}), flush=True)
+        b.record()
+        c, dd_ = _events()
+        c.record()
+        mr3.backward(w, Z, g, G)
+        dd_.record()
+        torch.cuda.synchronize()
+        tf.append(a.elapsed_time(b))
+        tb.append(c.elapsed_time(dd_))
+    wc = w.cpu().numpy()
+    fm, bm = statistics.median(tf), statistics.median(tb)
+    return {"metric": "backward / forward time (n=%d, all eigenpairs, FP64)" % n,
+            "value": bm / fm, "unit": "ratio", "forward_ms": fm, "backward_ms": bm,
+            "min_eigenvalue_gap": float(np.min(np.diff(wc))) if n > 1 else None}
 
 
-def _gpu_gates(d, e, w, Z, tnorm):
-    """Scaled residual max ||T z - lambda z|| / (n eps ||T||) and orthogonality
-    max |Z^T Z - I| / (n eps), computed with plain torch operations on the device."""
-    import torch
-    n = d.shape[0]
-    TZ = d[:, None] * Z
-    TZ[:-1] += e[:n - 1, None] * Z[1:]
-    TZ[1:] += e[:n - 1, None] * Z[:-1]
-    R = TZ - Z * w[None, :]
-    resid = torch.linalg.vector_norm(R, dim=0).max().item() / (n * EPS * tnorm)
-    G = Z.T @ Z
-    G.diagonal().sub_(1.0)
-    orth = G.abs().max().item() / (n * EPS)
-    return resid, orth
-
-
-def run_subset(args):
+def subset_leg(args):
     """Subset workload: eigenpairs 8001..12000 of the n = 20000 glued Wilkinson matrix (W21+
-    blocks glued by 1e-8), binary64 tree vs double-double tree.  Prints one JSON line."""
+    blocks glued by 1e-8), binary64 tree vs double-double tree, with the scaled residual and
+    orthogonality of each result."""
     import torch
     import paper_1401_4950_gb300 as mr3
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", torch.cuda.current_device())
     n, il, iu = 20000, 8001, 12000
     d, e = tm.make("glued_wilkinson", n)
     dt, et = torch.tensor(d, device=dev), torch.tensor(e, device=dev)
@@ -499,29 +560,30 @@ def run_subset(args):
     wn, _, _ = mr3.stemr(dt, et, rng="I", il=n, iu=n)
     tnorm = max(abs(w1.item()), abs(wn.item()))
     out = {"metric": "eigenpairs/s (n=20000 glued Wilkinson, eigenpairs 8001..12000)",
-           "unit": "eigenpairs/s", "config": {"workload": "MRRR subset, n=20000 glued W21+ "
-                                              "(e=1e-8 at joins), il=8001, iu=12000"}}
+           "unit": "eigenpairs/s", "config": "MRRR subset, n=20000 glued W21+ (e=1e-8 at "
+                                             "joins), il=8001, iu=12000"}
     for name, prec in (("fp64", mr3.FP64), ("dd", mr3.DD)):
         opts = mr3.make_opts(prec=prec, profile=1)
         for _ in range(2):
             mr3.stemr(dt, et, rng="I", il=il, iu=iu, opts=opts)
         torch.cuda.synchronize()
-        reps = max(1, args.steps)
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record()
+        reps = max(3, min(args.steps, 5))
+        a, b = _events()
+        a.record()
         for _ in range(reps):
             w, Z, info = mr3.stemr(dt, et, rng="I", il=il, iu=iu, opts=opts)
-        ev1.record()
+        b.record()
         torch.cuda.synchronize()
-        ms = ev0.elapsed_time(ev1) / reps
-        resid, orth = _gpu_gates(dt, et, w, Z, tnorm)
-        out[name] = {"value": (iu - il + 1) / (ms * 1e-3), "ms": ms, "resid": resid,
-                     "orth": orth, "dmax": info["dmax"], "nclusters": info["nclusters"],
-                     "largest_cluster": info["largest_cluster"],
+        ms = a.elapsed_time(b) / reps
+        resid, orth = gpu_gates(dt, et, w, Z, tnorm)
+        out[name] = {"value": (iu - il + 1) / (ms * 1e-3), "ms": ms, "resid": round(resid, 4),
+                     "orth": round(orth, 4), "dmax": info["dmax"],
+                     "nclusters": info["nclusters"], "largest_cluster": info["largest_cluster"],
                      "rqi_iters": info["rqi_iters"], "bisect_fallbacks": info["bisect_fallbacks"],
                      "status": info["status"],
                      "kernel_ms": [round(x, 3) for x in info["kernel_ms"]]}
-    print(json.dumps(out), flush=True)
+        del w, Z
+    return out
 
 
 def main():
@@ -534,34 +596,28 @@ def main():
     ap.add_argument("--n", type=int, default=None,
                     help="matrix order instead of the config's (smaller cases for ncu captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--batched", action="store_true",
-                    help="time the batched workload (one call vs per-matrix calls) instead")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline step only (no batched, backward and subset legs)")
     ap.add_argument("--batch", type=int, default=4096)
-    ap.add_argument("--backward", action="store_true",
-                    help="time the backward pass against the forward instead")
     ap.add_argument("--n-bwd", type=int, default=4096)
     ap.add_argument("--solver", default="batched", choices=["batched", "single"],
                     help="the step's matrices in one mr3_stemr_batched call, or one mr3_stemr "
                          "call each")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "dd"],
                     help="representation tree in binary64 or double-double (Ch. 5)")
-    ap.add_argument("--subset", action="store_true",
-                    help="time the n=20000 glued Wilkinson subset, binary64 vs double-double")
+    ap.add_argument("--leg", default=None, choices=["batched", "backward", "subset"],
+                    help="print only one of the extra legs as its own JSON line")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
         run_reference(args, args.config, rank)
         return
-    if args.batched:
-        run_batched(args)
-        return
-    if args.backward:
-        run_backward(args)
-        return
-    if args.subset:
-        run_subset(args)
+    if args.leg:
+        import torch
+        torch.cuda.set_device(0)
+        leg = {"batched": batched_leg, "backward": backward_leg, "subset": subset_leg}[args.leg]
+        print(json.dumps(leg(args)), flush=True)
         return
     run_gpu(args, args.config, rank, world)
 

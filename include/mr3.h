@@ -61,7 +61,10 @@ typedef enum { MR3_FP64 = 0, MR3_DD = 1 } mr3_precision;
 typedef struct {
     int prec;                  /* mr3_precision [MR3_FP64]                                   */
     double gaptol;             /* classification threshold on reldist (Sec. 3.2.3)
-                                  [1e-3 for FP64, 1e-10 for DD (Ch. 5, Eq. gaptolinterval)] */
+                                  [FP64: max(1e-3, min(2/n_b, 0.05)) for an irreducible
+                                  block of order n_b, so that the tree's loss of
+                                  orthogonality, ~eps/gaptol, stays below 10 n eps at small
+                                  n; DD: 1e-10 (Ch. 5, Eq. gaptolinterval)]               */
     unsigned long long seed;   /* stream of the root's random perturbation (Alg. MRRR)
                                   [0x5EED]                                                   */
     int max_rqi;               /* Rayleigh-quotient iterations per singleton before the
@@ -174,6 +177,20 @@ int mr3_stemr_batched(int nb, const long long *n_off, const double *d, const dou
                       const mr3_opts *opts, mr3_info *info, void *stream);
 
 /*
+ * mr3_stemr_batched_host -- mr3_stemr_batched on host arrays: the library copies d and e
+ * (n_off[nb] doubles each, packed as for mr3_stemr_batched) to the device, solves, and
+ * copies each matrix's m[b] eigenvalues to w[n_off[b] ..] and its n_b x m[b] eigenvectors
+ * to Z + z_off[b] (leading dimension n_b) in the caller's host arrays before returning.
+ * Arguments as for mr3_stemr_batched with host pointers for d, e, w and Z (pinned host
+ * memory is copied fastest); the device workspace, outputs included, comes from the
+ * library's pool and is returned to it.  Entries of w and Z beyond m[b] are not written.
+ */
+int mr3_stemr_batched_host(int nb, const long long *n_off, const double *d, const double *e,
+                           int range, const double *vl, const double *vu, const int *il,
+                           const int *iu, int *m, double *w, const long long *z_off, double *Z,
+                           const mr3_opts *opts, mr3_info *info, void *stream);
+
+/*
  * mr3_backward -- gradient of a scalar loss L(lambda, Z) with respect to d and e,
  * given the forward eigen-decomposition of T (all n eigenpairs) and the upstream
  * gradients g = dL/dlambda and G = dL/dZ.
@@ -209,8 +226,12 @@ int mr3_backward(int n, int k, const double *w, const double *Z, int ldz, const 
  *  Extra return code: MR3_ENOSCRATCH when n > MR3_STATIC_MAX_N (checked before any
  *  device work), or when the representation tree of this matrix needs more room than
  *  the array has (then w and Z are undefined, *m = 0, and the stream is idle on return).
- *  Set-up: the first call made with a device current looks up that device's array and
- *  caches its address; make that first call before beginning any stream capture.
+ *  Set-up: the first call made with a device current and n <= MR3_STATIC_MAX_N (n = 0
+ *  is enough) loads, on that device, every kernel this entry point launches and the
+ *  array itself (the runtime would otherwise load each kernel at its first launch, which
+ *  takes device memory), and looks up and caches the array's address.  A caller that
+ *  claims its device memory up front makes that first call before claiming it; the first
+ *  call on each device should also come before any stream capture begins.
  *  Sharing: one array per device.  Calls that overlap in time on the same device (other
  *  host threads, or streams not ordered with respect to each other) race on it: order them.
  */

@@ -8,7 +8,8 @@ built or loaded, every call raises.
 Entry points (same names as the C ABI):
   stemr(d, e, ...)             -> (w, Z, info)   device tensors in, device tensors out
   stemr_host(d, e, ...)        -> (w, Z, info)   numpy in, numpy out (copies inside the call)
-  stemr_batched(n_off, d, e, ...) -> (m, w, Z, info)
+  stemr_batched(n_off, d, e, ...) -> (m, w, Z, z_off, info)
+  stemr_batched_host(n_off, d, e, ...) -> (m, w, Z, z_off, info)  host arrays in and out
   backward(w, Z, gw, gZ)       -> (dbar, ebar)
   eigh_tridiagonal(d, e)       -> (w, Z) differentiable (torch.autograd.Function)
 """
@@ -80,6 +81,8 @@ def lib():
                                             vp, dp, ctypes.POINTER(Opts),
                                             ctypes.POINTER(Info), vp]
             L.mr3_stemr_batched.restype = c_int
+            L.mr3_stemr_batched_host.argtypes = L.mr3_stemr_batched.argtypes
+            L.mr3_stemr_batched_host.restype = c_int
             L.mr3_backward.argtypes = [c_int, c_int, dp, dp, c_int, dp, dp, c_int, dp, dp,
                                        ctypes.POINTER(Opts), vp]
             L.mr3_backward.restype = c_int
@@ -186,17 +189,23 @@ def stemr_static(d, e, rng="A", vl=0.0, vu=0.0, il=1, iu=None, opts=None, stream
         Zb = torch.empty((max(mcap, 1), max(n, 1)), dtype=torch.float64, device=d.device)
     else:
         w, Zb = out
-        assert w.dtype == torch.float64 and w.is_cuda and w.numel() >= mcap
+        assert (w.dtype == torch.float64 and w.is_cuda and w.is_contiguous()
+                and w.numel() >= mcap)
         assert (Zb.dtype == torch.float64 and Zb.is_cuda and Zb.is_contiguous()
                 and Zb.shape[0] >= mcap and Zb.shape[1] == max(n, 1))
+        # the library's array is the current device's: every operand lives on d's device
+        assert w.device == d.device and Zb.device == d.device
+    if n > 1:
+        assert e.device == d.device
     m = ctypes.c_int(0)
     info = Info()
     o = opts if opts is not None else make_opts()
-    rc = lib().mr3_stemr_static(n, ctypes.c_void_p(d.data_ptr()),
-                                ctypes.c_void_p(e.data_ptr() if n > 1 else 0), r, vl, vu, il,
-                                iu, ctypes.byref(m), ctypes.c_void_p(w.data_ptr()),
-                                ctypes.c_void_p(Zb.data_ptr()), max(n, 1), ctypes.byref(o),
-                                ctypes.byref(info), _stream_ptr(stream))
+    with torch.cuda.device(d.device):
+        rc = lib().mr3_stemr_static(n, ctypes.c_void_p(d.data_ptr()),
+                                    ctypes.c_void_p(e.data_ptr() if n > 1 else 0), r, vl, vu,
+                                    il, iu, ctypes.byref(m), ctypes.c_void_p(w.data_ptr()),
+                                    ctypes.c_void_p(Zb.data_ptr()), max(n, 1), ctypes.byref(o),
+                                    ctypes.byref(info), _stream_ptr(stream))
     _check(rc, "mr3_stemr_static")
     k = m.value
     res = info.as_dict()
@@ -269,6 +278,55 @@ def stemr_batched(n_off, d, e, rng="A", vl=None, vu=None, il=None, iu=None, opts
     out = info.as_dict()
     out["status"] = rc
     return m[:nb], w, Z, z_off, out
+
+
+def stemr_batched_host(n_off, d, e, rng="A", vl=None, vu=None, il=None, iu=None, opts=None,
+                       stream=None, out=None):
+    """mr3_stemr_batched_host: the packed batch on host arrays (numpy, or pinned CPU
+    tensors), copied in and out inside the call.  Returns (m, w, Z, z_off, info) with w and
+    Z host arrays laid out as for stemr_batched; `out` = (w, Z) reuses caller arrays
+    (float64, n_off[-1] and sum(n_b^2) entries)."""
+    n_off = np.ascontiguousarray(n_off, dtype=np.int64)
+    nb = n_off.shape[0] - 1
+    sizes = np.diff(n_off)
+    z_off = np.zeros(nb + 1, dtype=np.int64)
+    z_off[1:] = np.cumsum(sizes * sizes)
+
+    def host_ptr(a):
+        if hasattr(a, "data_ptr"):  # a CPU torch tensor (pinned memory is copied fastest)
+            assert a.device.type == "cpu" and a.is_contiguous() and str(a.dtype) == "torch.float64"
+            return ctypes.c_void_p(a.data_ptr())
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+        return a.ctypes.data_as(ctypes.c_void_p)
+
+    if out is None:
+        w = np.empty(max(int(n_off[-1]), 1))
+        Z = np.empty(max(int(z_off[-1]), 1))
+    else:
+        w, Z = out
+    keep = []
+
+    def ptr(a, dt):
+        if a is None:
+            return ctypes.c_void_p(0)
+        a = np.ascontiguousarray(a, dtype=dt)
+        keep.append(a)
+        return a.ctypes.data_as(ctypes.c_void_p)
+
+    r = _RANGES[rng] if isinstance(rng, str) else int(rng)
+    m = np.zeros(max(nb, 1), dtype=np.int32)
+    info = Info()
+    o = opts if opts is not None else make_opts()
+    rc = lib().mr3_stemr_batched_host(nb, n_off.ctypes.data_as(ctypes.c_void_p), host_ptr(d),
+                                      host_ptr(e), r, ptr(vl, np.float64), ptr(vu, np.float64),
+                                      ptr(il, np.int32), ptr(iu, np.int32),
+                                      m.ctypes.data_as(ctypes.c_void_p), host_ptr(w),
+                                      z_off.ctypes.data_as(ctypes.c_void_p), host_ptr(Z),
+                                      ctypes.byref(o), ctypes.byref(info), _stream_ptr(stream))
+    _check(rc, "mr3_stemr_batched_host")
+    res = info.as_dict()
+    res["status"] = rc
+    return m[:nb], w, Z, z_off, res
 
 
 def backward(w, Z, gw=None, gZ=None, opts=None, stream=None):

@@ -29,7 +29,7 @@ struct Opts {
 Opts resolve(const mr3_opts *o) {
     Opts r;
     r.prec = (o && o->prec == MR3_DD) ? MR3_DD : MR3_FP64;
-    r.gaptol = (o && o->gaptol > 0.0) ? o->gaptol : (r.prec == MR3_DD ? 1e-10 : 1e-3);
+    r.gaptol = (o && o->gaptol > 0.0) ? o->gaptol : (r.prec == MR3_DD ? 1e-10 : kGaptolAuto);
     r.seed = (o && o->seed) ? o->seed : 0x5EEDull;
     r.max_rqi = (o && o->max_rqi > 0) ? o->max_rqi : 10;
     r.max_tries = (o && o->max_shift_tries > 0) ? o->max_shift_tries : 8;
@@ -334,7 +334,9 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
     if (dd) launch_root_dd(nblk, blks, d, e, pool0, pool0_lo, o.seed, s);
     launch_init_columns(nblk, blks, nodes0, cnode, jloc, lo, hi, (int)ncols, s);
     prof.end(tk, 1, dd ? 3 : 2);
-    const double rtol = 1e-2 * o.gaptol;
+    // classification accuracy (Sec. 3.2.2): 1e-2 gaptol, with the smallest automatic
+    // gaptol (1e-3) standing in for the per-block choice
+    const double rtol = 1e-2 * (o.gaptol > 0.0 ? o.gaptol : 1e-3);
     if (range != MR3_RANGE_ALL) launch_outer_gaps(nblk, blks, nodes0, pool0, rtol, dinfo, s);
     bool any_multi = false;
     for (auto &M : mats) any_multi |= (M.nblk > 1 && M.m > 0);
@@ -691,6 +693,75 @@ int mr3_stemr_batched(int nb, const long long *n_off, const double *d, const dou
     }
     const int rc = solve(nb, mats, nrows, nrows, d, e, range, w, Z, o, info, (cudaStream_t)stream);
     for (int b = 0; b < nb; ++b) m[b] = mats[b].m;
+    return rc;
+}
+
+int mr3_stemr_batched_host(int nb, const long long *n_off, const double *d, const double *e,
+                           int range, const double *vl, const double *vu, const int *il,
+                           const int *iu, int *m, double *w, const long long *z_off, double *Z,
+                           const mr3_opts *opts, mr3_info *info, void *stream) {
+    if (nb < 0) return -1;
+    if (nb > 0 && !n_off) return -2;
+    if (nb == 0)
+        return mr3_stemr_batched(0, n_off, d, e, range, vl, vu, il, iu, m, w, z_off, Z, opts,
+                                 info, stream);
+    const long long nrows = n_off[nb];
+    if (n_off[0] != 0 || nrows < 0) return -2;
+    if (nrows > 0 && !d) return -3;
+    if (nrows > 0 && !e) return -4;
+    if (!m) return -10;
+    if (nrows > 0 && !w) return -11;
+    if (!z_off) return -12;
+    if (nrows > 0 && !Z) return -13;
+    long long zlen = 0; // Z elements: the furthest end of any matrix's block
+    for (int b = 0; b < nb; ++b) {
+        const long long nbk = n_off[b + 1] - n_off[b];
+        if (nbk < 0 || z_off[b] < 0) return nbk < 0 ? -2 : -12;
+        zlen = std::max(zlen, z_off[b] + nbk * nbk);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    double *dd = nullptr, *de = nullptr, *dw = nullptr, *dz = nullptr;
+    const size_t rows = (size_t)std::max<long long>(nrows, 1);
+    int rc = 0;
+    if (lib_malloc_async((void **)&dd, sizeof(double) * rows, s) != cudaSuccess ||
+        lib_malloc_async((void **)&de, sizeof(double) * rows, s) != cudaSuccess ||
+        lib_malloc_async((void **)&dw, sizeof(double) * rows, s) != cudaSuccess ||
+        lib_malloc_async((void **)&dz, sizeof(double) * (size_t)std::max<long long>(zlen, 1), s) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        rc = MR3_EOOM;
+    }
+    if (!rc && nrows > 0) {
+        if (cudaMemcpyAsync(dd, d, sizeof(double) * nrows, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(de, e, sizeof(double) * nrows, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+            cudaGetLastError();
+            rc = MR3_ECUDA;
+        }
+    }
+    if (!rc) {
+        rc = mr3_stemr_batched(nb, n_off, dd, de, range, vl, vu, il, iu, m, dw, z_off, dz, opts,
+                               info, stream);
+        if (rc >= 0 && rc != MR3_EOOM && rc != MR3_ECUDA) {
+            // eigenvalues of matrix b at w[n_off[b] ..], its m[b] eigenvectors at Z + z_off[b]
+            // (leading dimension n_b): one copy per matrix for w and for Z
+            for (int b = 0; b < nb && !rc; ++b) {
+                const long long nbk = n_off[b + 1] - n_off[b];
+                if (m[b] <= 0) continue;
+                if (cudaMemcpyAsync(w + n_off[b], dw + n_off[b], sizeof(double) * m[b],
+                                    cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                    cudaMemcpyAsync(Z + z_off[b], dz + z_off[b], sizeof(double) * nbk * m[b],
+                                    cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+                    cudaGetLastError();
+                    rc = MR3_ECUDA;
+                }
+            }
+        }
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) { cudaGetLastError(); rc = MR3_ECUDA; }
+    if (dd) cudaFreeAsync(dd, s);
+    if (de) cudaFreeAsync(de, s);
+    if (dw) cudaFreeAsync(dw, s);
+    if (dz) cudaFreeAsync(dz, s);
     return rc;
 }
 

@@ -19,7 +19,8 @@ def _declared():
 
 def test_header_declares_the_boundary():
     names = _declared()
-    for required in ("mr3_stemr", "mr3_stemr_batched", "mr3_backward", "mr3_stemr_host"):
+    for required in ("mr3_stemr", "mr3_stemr_batched", "mr3_backward", "mr3_stemr_host",
+                     "mr3_stemr_batched_host"):
         assert required in names
 
 
