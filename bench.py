@@ -424,6 +424,7 @@ def run_gpu(args, cfg, rank, world):
         extras["batched"] = batched_leg(args)
         extras["backward"] = backward_leg(args)
         extras["subset"] = subset_leg(args)
+        extras["left_subsets"] = left_subset_leg(args)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(mats)
@@ -586,6 +587,41 @@ def subset_leg(args):
     return out
 
 
+def left_subset_leg(args):
+    """Ch. 4 subset experiment: eigenpairs 1..iu at the left end of the spectrum of order
+    10,001 matrices (1-2-1, Wilkinson, uniform(-1,1)), time against the fraction iu / n.
+    MRRR's cost is proportional to the number of eigenpairs computed; reported as the
+    median device time per fraction and its ratio to the time for all eigenpairs."""
+    import torch
+    import paper_1401_4950_gb300 as mr3
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = 10001
+    fracs = (0.01, 0.1, 0.25, 0.5, 1.0)
+    out = {"metric": "left-end subset time against the fraction of eigenpairs (n=10001)",
+           "unit": "ms", "fractions": list(fracs)}
+    for kind, seeds in (("one_two_one", None), ("wilkinson", None), ("random", (601, 602))):
+        d, e = tm.random_uniform(n, *seeds) if seeds else tm.make(kind, n)
+        dt, et = torch.tensor(d, device=dev), torch.tensor(e, device=dev)
+        times = []
+        for f in fracs:
+            iu = max(1, int(round(f * n)))
+            for _ in range(2):
+                mr3.stemr(dt, et, rng="I", il=1, iu=iu)
+            tt = []
+            for _ in range(3):
+                a, b = _events()
+                a.record()
+                w, Z, _ = mr3.stemr(dt, et, rng="I", il=1, iu=iu)
+                b.record()
+                torch.cuda.synchronize()
+                tt.append(a.elapsed_time(b))
+                del w, Z
+            times.append(statistics.median(tt))
+        out[kind] = {"ms": [round(t, 3) for t in times],
+                     "relative_to_all": [round(t / times[-1], 4) for t in times]}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -605,7 +641,8 @@ def main():
                          "call each")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "dd"],
                     help="representation tree in binary64 or double-double (Ch. 5)")
-    ap.add_argument("--leg", default=None, choices=["batched", "backward", "subset"],
+    ap.add_argument("--leg", default=None,
+                    choices=["batched", "backward", "subset", "left_subsets"],
                     help="print only one of the extra legs as its own JSON line")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -616,7 +653,8 @@ def main():
     if args.leg:
         import torch
         torch.cuda.set_device(0)
-        leg = {"batched": batched_leg, "backward": backward_leg, "subset": subset_leg}[args.leg]
+        leg = {"batched": batched_leg, "backward": backward_leg, "subset": subset_leg,
+               "left_subsets": left_subset_leg}[args.leg]
         print(json.dumps(leg(args)), flush=True)
         return
     run_gpu(args, args.config, rank, world)

@@ -743,8 +743,10 @@ int mr3_stemr_batched_host(int nb, const long long *n_off, const double *d, cons
                                info, stream);
         if (rc >= 0 && rc != MR3_EOOM && rc != MR3_ECUDA) {
             // eigenvalues of matrix b at w[n_off[b] ..], its m[b] eigenvectors at Z + z_off[b]
-            // (leading dimension n_b): one copy per matrix for w and for Z
-            for (int b = 0; b < nb && !rc; ++b) {
+            // (leading dimension n_b): one copy per matrix for w and for Z.  rc may hold a
+            // positive status (a warning): the results are copied all the same.
+            bool copy_failed = false;
+            for (int b = 0; b < nb && !copy_failed; ++b) {
                 const long long nbk = n_off[b + 1] - n_off[b];
                 if (m[b] <= 0) continue;
                 if (cudaMemcpyAsync(w + n_off[b], dw + n_off[b], sizeof(double) * m[b],
@@ -752,9 +754,10 @@ int mr3_stemr_batched_host(int nb, const long long *n_off, const double *d, cons
                     cudaMemcpyAsync(Z + z_off[b], dz + z_off[b], sizeof(double) * nbk * m[b],
                                     cudaMemcpyDeviceToHost, s) != cudaSuccess) {
                     cudaGetLastError();
-                    rc = MR3_ECUDA;
+                    copy_failed = true;
                 }
             }
+            if (copy_failed) rc = MR3_ECUDA;
         }
     }
     if (cudaStreamSynchronize(s) != cudaSuccess) { cudaGetLastError(); rc = MR3_ECUDA; }

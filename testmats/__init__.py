@@ -18,6 +18,10 @@ workloads it measures:
   * glued Wilkinson -- W21+ blocks (d = |j - 10|, j = i mod 21) with e = 1 inside a
                     block and a small glue value between blocks (ref. "glued" in Ch. 3)
   * Clement, Legendre, Laguerre, Hermite (App. D)
+  * Uniform and Geometric (App. D) -- tridiagonals with a prescribed spectrum
+                    lambda_k = eps + (k-1)(1-eps)/(n-1) and lambda_k = eps^((n-k)/(n-1)),
+                    eps = 2^-53, built by Lanczos with full reorthogonalisation on
+                    diag(lambda) from a seeded random start vector
   * uniform random -- d_i, e_i i.i.d. uniform(-1, 1)
 """
 from __future__ import annotations
@@ -109,6 +113,77 @@ def hermite(n: int):
     return np.zeros(n), np.sqrt(np.arange(1, n, dtype=np.float64))
 
 
+UNIT_ROUNDOFF = 2.0 ** -53
+
+
+def uniform_spectrum(n: int) -> np.ndarray:
+    """App. D, Uniform: lambda_k = eps + (k-1)(1-eps)/(n-1), k = 1..n."""
+    if n == 1:
+        return np.array([UNIT_ROUNDOFF])
+    k = np.arange(1, n + 1, dtype=np.float64)
+    return UNIT_ROUNDOFF + (k - 1) * (1.0 - UNIT_ROUNDOFF) / (n - 1)
+
+
+def geometric_spectrum(n: int) -> np.ndarray:
+    """App. D, Geometric: lambda_k = eps^((n-k)/(n-1)), k = 1..n."""
+    if n == 1:
+        return np.array([1.0])
+    k = np.arange(1, n + 1, dtype=np.float64)
+    return UNIT_ROUNDOFF ** ((n - k) / (n - 1))
+
+
+def lanczos_tridiagonal(lam, seed: int = 7001, device=None):
+    """A symmetric tridiagonal T = Q^T diag(lam) Q with the eigenvalues lam (up to rounding):
+    n steps of Lanczos on diag(lam) from a seeded normal start vector, with full
+    reorthogonalisation (classical Gram-Schmidt applied twice) against every earlier
+    Lanczos vector.  Returns (d, e).  With `device` (a torch device) the vectors live
+    there; the output is a numpy array either way."""
+    lam = np.asarray(lam, dtype=np.float64)
+    n = lam.shape[0]
+    if device is None:
+        xp_lam = lam
+        Q = np.zeros((n, n))
+        q = normal(seed, n)
+        dot = np.dot
+
+        def mv(A, x):
+            return A @ x
+    else:
+        import torch
+        xp_lam = torch.tensor(lam, device=device)
+        Q = torch.zeros((n, n), dtype=torch.float64, device=device)
+        q = torch.tensor(normal(seed, n), device=device)
+        dot = torch.dot
+
+        def mv(A, x):
+            return A @ x
+    q = q / float(dot(q, q)) ** 0.5
+    d = np.zeros(n)
+    e = np.zeros(max(n - 1, 0))
+    for j in range(n):
+        Q[j] = q
+        w = xp_lam * q
+        d[j] = float(dot(q, w))
+        for _ in range(2):  # full reorthogonalisation, twice
+            w = w - mv(Q[: j + 1].T, mv(Q[: j + 1], w))
+        if j == n - 1:
+            break
+        b = float(dot(w, w)) ** 0.5
+        e[j] = b
+        if b == 0.0:  # invariant subspace (cannot happen with distinct lam and a generic start)
+            raise ValueError("Lanczos breakdown at step %d" % j)
+        q = w / b
+    return d, e
+
+
+def uniform_eigs(n: int, seed: int = 7001, device=None):
+    return lanczos_tridiagonal(uniform_spectrum(n), seed, device)
+
+
+def geometric_eigs(n: int, seed: int = 7002, device=None):
+    return lanczos_tridiagonal(geometric_spectrum(n), seed, device)
+
+
 FAMILIES = {
     "one_two_one": one_two_one,
     "wilkinson": wilkinson,
@@ -117,6 +192,8 @@ FAMILIES = {
     "legendre": legendre,
     "laguerre": laguerre,
     "hermite": hermite,
+    "uniform_eigs": uniform_eigs,
+    "geometric_eigs": geometric_eigs,
 }
 
 

@@ -117,3 +117,41 @@ def test_batched_bench_step(cuda):
     mats_out, out, info = _batched([8192, 8192, 8192], fill=lambda b, n: mats[b])
     for (d, e), (wb, Zb), gate in zip(mats, out, gates):
         check_eigenpairs(d, e, wb, Zb, orth_gate=gate, vec_compare=False)
+
+
+@pytest.mark.parametrize("rng", ["A", "I"])
+def test_batched_host_matches_device_call(cuda, rng):
+    # mr3_stemr_batched_host (host buffers, copies inside the call) returns exactly what the
+    # device call returns on the same packed batch, an empty matrix included
+    import torch
+    import paper_1401_4950_gb300 as mr3
+    sizes = [37, 0, 300, 1, 129, 64]
+    n_off = np.zeros(len(sizes) + 1, dtype=np.int64)
+    n_off[1:] = np.cumsum(sizes)
+    d = np.empty(n_off[-1])
+    e = np.zeros(n_off[-1])
+    for b, n in enumerate(sizes):
+        db, eb = tm.random_uniform(n, 700 + 2 * b, 701 + 2 * b)
+        d[n_off[b]:n_off[b + 1]] = db
+        e[n_off[b]:n_off[b + 1] - 1] = eb
+    kw = {}
+    if rng == "I":
+        kw = {"il": [max(1, n // 3) if n else 1 for n in sizes],
+              "iu": [max(1, (2 * n) // 3) if n else 0 for n in sizes]}
+        kw["il"] = [1 if n == 0 else a for a, n in zip(kw["il"], sizes)]
+    m0, w0, Z0, z_off, _ = mr3.stemr_batched(n_off, torch.tensor(d, device="cuda"),
+                                             torch.tensor(e, device="cuda"), rng=rng, **kw)
+    torch.cuda.synchronize()
+    m1, w1, Z1, z_off1, _ = mr3.stemr_batched_host(n_off, d, e, rng=rng, **kw)
+    assert np.array_equal(m0, m1) and np.array_equal(z_off, z_off1)
+    w0, Z0 = w0.cpu().numpy(), Z0.cpu().numpy()
+    for b, n in enumerate(sizes):
+        k = int(m0[b])
+        assert np.array_equal(w1[n_off[b]:n_off[b] + k], w0[n_off[b]:n_off[b] + k])
+        assert np.array_equal(Z1[z_off[b]:z_off[b] + n * k], Z0[z_off[b]:z_off[b] + n * k])
+        if k:
+            db, eb = d[n_off[b]:n_off[b + 1]], e[n_off[b]:n_off[b + 1] - 1]
+            il = kw["il"][b] if kw else 1
+            check_eigenpairs(db, eb, w1[n_off[b]:n_off[b] + k],
+                             Z1[z_off[b]:z_off[b] + n * k].reshape(k, n).T, il=il,
+                             iu=il + k - 1, vec_compare=False)

@@ -23,7 +23,7 @@ def _solve(d, e, prec, **kw):
 CASES = [("random", 1), ("random", 2), ("random", 37), ("random", 1000), ("one_two_one", 1000),
          ("wilkinson", 21), ("wilkinson", 1001), ("glued_wilkinson", 42),
          ("glued_wilkinson", 1000), ("clement", 501), ("legendre", 300), ("laguerre", 300),
-         ("hermite", 400)]
+         ("hermite", 400), ("uniform_eigs", 300), ("geometric_eigs", 1000)]
 
 
 @pytest.mark.parametrize("kind,n", CASES)

@@ -23,7 +23,8 @@ CASES = [("random", 1), ("random", 2), ("random", 3), ("random", 10), ("random",
          ("random", 100), ("random", 1000), ("one_two_one", 2), ("one_two_one", 100),
          ("one_two_one", 1000), ("wilkinson", 21), ("wilkinson", 64), ("wilkinson", 1001),
          ("glued_wilkinson", 42), ("glued_wilkinson", 1000), ("clement", 50), ("clement", 501),
-         ("legendre", 300), ("laguerre", 300), ("hermite", 400)]
+         ("legendre", 300), ("laguerre", 300), ("hermite", 400), ("uniform_eigs", 300),
+         ("uniform_eigs", 1000), ("geometric_eigs", 300), ("geometric_eigs", 1000)]
 
 
 # Every family is held to the 10 n eps orthogonality gate.  The binary64 tree's loss of

@@ -196,3 +196,19 @@ def test_clement_vectors_with_zero_eigenvalue(n):
     assert np.all(np.isfinite(Z))
     assert M.scaled_residual(d, e, w, Z, n - 1.0) <= 10
     assert M.scaled_orthogonality(Z) <= 10
+
+
+@pytest.mark.parametrize("kind,n", [("uniform_eigs", 9), ("uniform_eigs", 200), ("uniform_eigs", 600),
+                                    ("geometric_eigs", 9), ("geometric_eigs", 200),
+                                    ("geometric_eigs", 600)])
+def test_prescribed_spectra_of_app_d(kind, n):
+    # App. D, Uniform and Geometric: T is built by Lanczos (full reorthogonalisation) on
+    # diag(lambda) with the printed spectrum, so the spectrum is known in closed form; the
+    # oracle's bisection must return it to ~n eps ||T|| (||T|| = 1)
+    d, e = tm.make(kind, n)
+    lam = tm.uniform_spectrum(n) if kind == "uniform_eigs" else tm.geometric_spectrum(n)
+    w = oracle.eigvals(d, e)
+    assert np.max(np.abs(w - lam)) <= 4 * n * EPS
+    if n <= 64:
+        wj, _ = oracle.jacobi(oracle.dense(d, e))
+        assert np.max(np.abs(wj - lam)) <= 50 * n * EPS
