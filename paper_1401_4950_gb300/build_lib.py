@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmr3.so")
 
 SOURCES = ["mr3_prologue.cu", "mr3_levels.cu", "mr3_rqi.cu", "mr3_api.cu", "mr3_backward.cu",
-           "mr3_static.cu", "mr3_ddpath.cu"]
+           "mr3_static.cu", "mr3_ddpath.cu", "mr3_tc_gemm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 
@@ -30,11 +30,6 @@ def _nvcc() -> str:
         if cand and os.path.exists(cand):
             return cand
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libmr3")
-
-
-def _cuda_libdir(nvcc: str) -> str:
-    """lib64 of the toolkit that holds nvcc (cuBLAS is loaded from there)."""
-    return os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
 
 
 def _stale(target: str, deps) -> bool:
@@ -74,8 +69,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + ".%d.tmp" % os.getpid()
-        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static", "-lcublas",
-             "-Xlinker", "-rpath," + _cuda_libdir(nvcc)])
+        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"])
         os.replace(tmp, LIB)
     return LIB
 

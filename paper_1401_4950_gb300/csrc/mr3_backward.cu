@@ -21,11 +21,12 @@
 // most 2^(24 - 2 beta) terms is an integer below 2^24 and comes out of an FP32-accumulating
 // GEMM exactly; the slice products whose weight 2^(-beta (p + q)) is below 2^(-beta (s+1))
 // are dropped (their sum is below 2^-54 of the scale), and the rest is summed in binary64.
-// The slice GEMMs are plain cuBLAS bf16 GEMMs.
+// The slice GEMMs run on the library's own tcgen05 kernel (mr3_tc_gemm.cu): slice planes
+// are stored K-major with a leading dimension padded to a multiple of 64 elements (the
+// left operand of Y = Z B written transposed), so both operands load by TMA.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
-#include <cublas_v2.h>
 #include "mr3.h"
 #include "mr3_kernels.h"
 
@@ -169,19 +170,21 @@ __global__ void k_line_exponent(int n, const unsigned long long *__restrict__ mx
 // Slices of X (n x n, column-major) by integer arithmetic: |x| 2^-e < 1 is read as the
 // 64-bit fixed-point fraction F (its bits below 2^-64 truncated), slice p is bits
 // [64 - beta (p+1), 64 - beta p) of F with the sign of x, an integer of magnitude < 2^beta,
-// written as bf16 to plane S[p] (column-major, leading dimension n).  Hence
-// x 2^-e = sum_p a_p 2^(-beta (p+1)) + r with |r| < 2^(-beta s).
+// written as bf16 to plane S[p] (n x ldp elements): entry (r, c) at c ldp + r, or at
+// r ldp + c with trans_out.  Hence x 2^-e = sum_p a_p 2^(-beta (p+1)) + r with
+// |r| < 2^(-beta s).
 __global__ void k_slice(int n, const double *__restrict__ X, int ldx, const int *__restrict__ ex,
-                        bool by_row, int beta, int s, unsigned short *S) {
+                        bool by_row, int beta, int s, int ldp, bool trans_out, unsigned short *S) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)n * n) return;
     const int c = (int)(idx / n), r = (int)(idx % n);
     const unsigned long long bits = (unsigned long long)__double_as_longlong(X[(size_t)c * ldx + r]);
     const unsigned sgn = (unsigned)(bits >> 63) << 15;
     const int eb = (int)((bits >> 52) & 0x7ff);
-    const size_t plane = (size_t)n * n;
+    const size_t plane = (size_t)n * ldp;
+    const size_t o = trans_out ? (size_t)r * ldp + c : (size_t)c * ldp + r;
     if (eb == 0x7ff) { // NaN or infinity: propagate a NaN through the products
-        for (int p = 0; p < s; ++p) S[p * plane + idx] = (unsigned short)0x7fc0;
+        for (int p = 0; p < s; ++p) S[p * plane + o] = (unsigned short)0x7fc0;
         return;
     }
     const unsigned long long m = eb ? ((bits & 0xfffffffffffffull) | (1ull << 52)) : (bits & 0xfffffffffffffull);
@@ -196,7 +199,7 @@ __global__ void k_slice(int n, const double *__restrict__ X, int ldx, const int 
             const int e2 = 31 - __clz((int)v);
             h = (unsigned short)(sgn | ((unsigned)(e2 + 127) << 7) | ((v << (7 - e2)) & 0x7fu));
         }
-        S[p * plane + idx] = h;
+        S[p * plane + o] = h;
     }
 }
 
@@ -241,38 +244,22 @@ __global__ void k_ozaki_finish_scale(int n, const int *__restrict__ ea, const in
     acc[idx] = scale2(acc[idx], ea[j] + eb[k]);
 }
 
-// One cuBLAS handle per device, created on first use; the mutex serialises its users.
-std::mutex g_blas_mutex;
-cublasHandle_t g_blas[64] = {};
-
-cublasHandle_t blas_for_current_device() {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-    if (!g_blas[dev] && cublasCreate(&g_blas[dev]) != CUBLAS_STATUS_SUCCESS) g_blas[dev] = nullptr;
-    return g_blas[dev];
-}
-
-// acc = op(A) * B summed exactly slice by slice; transA: op(A) = A^T with A's columns
-// scaled, else op(A) = A with A's rows scaled; B's columns scaled.  SA, SB: s planes of
-// n x n bf16 each; Cbuf: n x s n floats.
-int ozaki_product(cublasHandle_t h, int n, const OzakiPlan &pl, bool transA,
-                  const unsigned short *SA, const unsigned short *SB, float *Cbuf, double *acc,
-                  cudaStream_t st) {
-    const size_t plane = (size_t)n * n;
-    const unsigned nblk = (unsigned)((plane + 255) / 256);
-    const float one = 1.f, zero = 0.f;
-    if (cudaMemsetAsync(acc, 0, sizeof(double) * plane, st) != cudaSuccess) return MR3_ECUDA;
+// acc = op(A) * B summed exactly slice by slice: A_p (s planes, K-major, leading dimension
+// ldp: row m of op(A) at A_p + m ldp), B (s planes of n columns side by side, column j of
+// the wide operand at B + j ldp); Cbuf: n x s n floats.  Slice p of A meets slices
+// q < s - p of B in one tensor-core product per contraction chunk.
+int ozaki_product(int n, int ldp, const OzakiPlan &pl, const unsigned short *SA,
+                  const unsigned short *SB, float *Cbuf, double *acc, int *err, cudaStream_t st) {
+    const size_t plane = (size_t)n * ldp;
+    const unsigned nblk = (unsigned)(((size_t)n * n + 255) / 256);
+    if (cudaMemsetAsync(acc, 0, sizeof(double) * n * n, st) != cudaSuccess) return MR3_ECUDA;
     for (int c0 = 0; c0 < n; c0 += pl.chunk) {
         const int kc = std::min(pl.chunk, n - c0);
         for (int p = pl.s - 1; p >= 0; --p) {
             const int nq = pl.s - p; // slices q with p + q <= s - 1
-            const unsigned short *A = SA + p * plane + (transA ? (size_t)c0 : (size_t)c0 * n);
-            const unsigned short *B = SB + c0;
-            const cublasStatus_t rc = cublasGemmEx(
-                h, transA ? CUBLAS_OP_T : CUBLAS_OP_N, CUBLAS_OP_N, n, nq * n, kc, &one, A,
-                CUDA_R_16BF, n, B, CUDA_R_16BF, n, &zero, Cbuf, CUDA_R_32F, n,
-                CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
-            if (rc != CUBLAS_STATUS_SUCCESS) return MR3_ECUDA;
+            if (tc_gemm_bf16(n, nq * n, n, c0, c0 + kc, SA + p * plane, ldp, SB, ldp, Cbuf, n,
+                             err, st))
+                return MR3_ECUDA;
             k_ozaki_accumulate<<<nblk, 256, 0, st>>>(n, nq, p, pl.beta, Cbuf, acc);
         }
     }
@@ -347,12 +334,16 @@ int vector_part_ozaki(int n, const double *w, const double *Z, int ldz, const do
                       int ldgz, double delta, double *Y, cudaStream_t st) {
     const OzakiPlan pl = ozaki_plan(n);
     const size_t plane = (size_t)n * n;
+    const int ldp = (n + 63) / 64 * 64; // slice planes: leading dimension a multiple of 64
+    const size_t splane = (size_t)n * ldp;
     unsigned short *SA = nullptr, *SB = nullptr;
     float *Cbuf = nullptr;
     double *acc = nullptr;
     int *ex = nullptr;
     unsigned long long *mx = nullptr;
+    int *err = nullptr;
     auto done = [&](int code) {
+        if (err) cudaFreeAsync(err, st);
         if (SA) cudaFreeAsync(SA, st);
         if (SB) cudaFreeAsync(SB, st);
         if (Cbuf) cudaFreeAsync(Cbuf, st);
@@ -361,8 +352,9 @@ int vector_part_ozaki(int n, const double *w, const double *Z, int ldz, const do
         if (mx) cudaFreeAsync(mx, st);
         return code;
     };
-    if (lib_malloc_async((void **)&SA, sizeof(unsigned short) * plane * pl.s, st) != cudaSuccess ||
-        lib_malloc_async((void **)&SB, sizeof(unsigned short) * plane * pl.s, st) != cudaSuccess ||
+    if (lib_malloc_async((void **)&SA, sizeof(unsigned short) * splane * pl.s, st) != cudaSuccess ||
+        lib_malloc_async((void **)&SB, sizeof(unsigned short) * splane * pl.s, st) != cudaSuccess ||
+        lib_malloc_async((void **)&err, sizeof(int), st) != cudaSuccess ||
         lib_malloc_async((void **)&Cbuf, sizeof(float) * plane * pl.s, st) != cudaSuccess ||
         lib_malloc_async((void **)&acc, sizeof(double) * plane, st) != cudaSuccess ||
         lib_malloc_async((void **)&ex, sizeof(int) * 4 * n, st) != cudaSuccess ||
@@ -375,18 +367,18 @@ int vector_part_ozaki(int n, const double *w, const double *Z, int ldz, const do
     const unsigned nblk = (unsigned)((plane + 255) / 256);
     const unsigned rblk = (unsigned)((n + 127) / 128);
     const dim3 mgrid((n + 31) / 32, (n + 255) / 256);
-    if (cudaMemsetAsync(mx, 0, sizeof(unsigned long long) * 4 * n, st) != cudaSuccess) return done(MR3_ECUDA);
-    std::lock_guard<std::mutex> lock(g_blas_mutex);
-    cublasHandle_t h = blas_for_current_device();
-    if (!h || cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS) return done(MR3_ECUDA);
+    if (cudaMemsetAsync(mx, 0, sizeof(unsigned long long) * 4 * n, st) != cudaSuccess ||
+        cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess)
+        return done(MR3_ECUDA);
     // C = Z^T G: columns of Z and of G scaled
     k_line_max<<<mgrid, 256, 0, st>>>(n, Z, ldz, false, ma);
     k_line_max<<<mgrid, 256, 0, st>>>(n, gZ, ldgz, false, mb);
     k_line_exponent<<<rblk, 128, 0, st>>>(n, ma, ea);
     k_line_exponent<<<rblk, 128, 0, st>>>(n, mb, eb);
-    k_slice<<<nblk, 256, 0, st>>>(n, Z, ldz, ea, false, pl.beta, pl.s, SA);
-    k_slice<<<nblk, 256, 0, st>>>(n, gZ, ldgz, eb, false, pl.beta, pl.s, SB);
-    int rc = ozaki_product(h, n, pl, true, SA, SB, Cbuf, acc, st);
+    // op(A) = Z^T: row m of Z^T is column m of Z (K-major as stored)
+    k_slice<<<nblk, 256, 0, st>>>(n, Z, ldz, ea, false, pl.beta, pl.s, ldp, false, SA);
+    k_slice<<<nblk, 256, 0, st>>>(n, gZ, ldgz, eb, false, pl.beta, pl.s, ldp, false, SB);
+    int rc = ozaki_product(n, ldp, pl, SA, SB, Cbuf, acc, err, st);
     if (rc) return done(rc);
     k_ozaki_finish_F<<<nblk, 256, 0, st>>>(n, ea, eb, w, delta, acc);
     // Y = Z B: rows of Z and columns of B scaled
@@ -394,11 +386,15 @@ int vector_part_ozaki(int n, const double *w, const double *Z, int ldz, const do
     k_line_max<<<mgrid, 256, 0, st>>>(n, acc, n, false, mb2);
     k_line_exponent<<<rblk, 128, 0, st>>>(n, ma2, ea2);
     k_line_exponent<<<rblk, 128, 0, st>>>(n, mb2, eb2);
-    k_slice<<<nblk, 256, 0, st>>>(n, Z, ldz, ea2, true, pl.beta, pl.s, SA);
-    k_slice<<<nblk, 256, 0, st>>>(n, acc, n, eb2, false, pl.beta, pl.s, SB);
-    rc = ozaki_product(h, n, pl, false, SA, SB, Cbuf, Y, st);
+    // op(A) = Z: its slices written transposed so that row m of Z is contiguous
+    k_slice<<<nblk, 256, 0, st>>>(n, Z, ldz, ea2, true, pl.beta, pl.s, ldp, true, SA);
+    k_slice<<<nblk, 256, 0, st>>>(n, acc, n, eb2, false, pl.beta, pl.s, ldp, false, SB);
+    rc = ozaki_product(n, ldp, pl, SA, SB, Cbuf, Y, err, st);
     if (rc) return done(rc);
     k_ozaki_finish_scale<<<nblk, 256, 0, st>>>(n, ea2, eb2, Y);
+    // a tensor-core product whose pipeline gave up leaves the error flag set
+    int herr = 0;
+    if (read_back(&herr, err, sizeof(int), st) != cudaSuccess || herr) return done(MR3_ECUDA);
     return done(0);
 }
 

@@ -106,6 +106,18 @@ template <class... K> cudaError_t load_kernels(K... k) {
     }
     return err;
 }
+// Copies bytes from device memory to host memory in stream order and waits for them
+// (mr3_api.cu: through a mapped pinned buffer, no copy engine).
+cudaError_t read_back(void *dst, const void *src, size_t bytes, cudaStream_t s);
+// C (M x N, FP32, column-major, ldc) = sum_{k0 <= k < k1} A[m, k] B[k, j] on the tensor
+// cores (mr3_tc_gemm.cu): bf16 operands, both K-major (A row m at A + m lda, B column j at
+// B + j ldb, K extent K), lda and ldb multiples of 64, k0 a multiple of 64, 16-byte aligned
+// bases; products exact while every chunk sum is an integer below 2^24.  Returns 0, or -1
+// when the arguments or the launch are rejected; *err (device) is set to 1 when a wait in
+// the kernel gave up.
+int tc_gemm_bf16(int M, int N, int K, int k0, int k1, const unsigned short *A, int lda,
+                 const unsigned short *B, int ldb, float *C, int ldc, int *err, cudaStream_t s);
+cudaError_t preload_tc_gemm();
 cudaError_t preload_prologue();
 cudaError_t preload_levels();
 cudaError_t preload_rqi();

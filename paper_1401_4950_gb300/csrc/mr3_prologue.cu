@@ -468,8 +468,12 @@ __device__ void factor_root(int n, const double *__restrict__ d, const double *_
 // One warp per block.  (1) Rough extremal eigenvalues of T by 16-point multisection with
 // FP32 Sturm counts (lanes 0-15: lambda_1, lanes 16-31: lambda_n).  (2) Candidate root
 // shifts mu_L = lambda_1 - delta and mu_R = lambda_n + delta, delta = max(4 n eps ||T||,
-// 2 width); both FP64 factorizations are computed (lanes 0, 1); the definite one with
-// the smaller element growth wins, ties to the left; if neither is definite delta doubles
+// 2 width); both FP64 factorizations are computed (lanes 0, 1).  When both are definite
+// the end holding clearly more eigenvalues wins (a 5:4 majority of the Sturm count at the
+// middle of the spectrum): shifting next to the dense part keeps its relative gaps large,
+// so fewer eigenvalues cluster; otherwise the smaller element growth, ties to the left
+// (definite factorizations have no large element growth either way).  If neither is
+// definite delta doubles
 // (at most 10 tries, then mu = gl - spdiam/8 which is always definite).  (3) The chosen
 // factorization's primary data d, l are perturbed by relative amounts xi u, xi = 8 eps,
 // u uniform in (-1, 1) from SplitMix64 (Alg. MRRR, perturbation of the root), and dl, dll
@@ -508,6 +512,11 @@ __global__ void k_root(int nblk, BlkDesc *blks, const double *__restrict__ D,
     }
     const double L1 = __shfl_sync(FULL_MASK, L, 0), H1 = __shfl_sync(FULL_MASK, H, 0);
     const double Ln = __shfl_sync(FULL_MASK, L, 16), Hn = __shfl_sync(FULL_MASK, H, 16);
+    // eigenvalues below the middle of the spectrum (binary32 count, one lane)
+    int cmid = 0;
+    if (lane == 0) cmid = negcount_T_f32(n, af, b2f, (float)(0.5 * (L1 + Hn)));
+    cmid = __shfl_sync(FULL_MASK, cmid, 0);
+    const int pref = (4 * cmid > 5 * (n - cmid)) ? 0 : ((4 * (n - cmid) > 5 * cmid) ? 1 : -1);
     const double tn = fmax(fabs(B.gl), fabs(B.gu));
     // the single-precision counts are exact for T perturbed by ~eps_32 |T| entrywise
     const double d32 = 4.0 * 0x1p-24 * tn;
@@ -532,7 +541,8 @@ __global__ void k_root(int nblk, BlkDesc *blks, const double *__restrict__ D,
         const double g0 = __shfl_sync(FULL_MASK, g, 0), g1 = __shfl_sync(FULL_MASK, g, 1);
         if (ok0 || ok1) {
             found = true;
-            if (ok0 && (!ok1 || g0 <= g1)) { mu = muL; src = reg0; kofs = 0; }
+            const bool left = (ok0 && ok1) ? (pref == 0 || (pref < 0 && g0 <= g1)) : (ok0 != 0);
+            if (left) { mu = muL; src = reg0; kofs = 0; }
             else { mu = muR; src = reg1; kofs = 1; }
         } else {
             dL *= 2.0;
