@@ -214,6 +214,30 @@ int mr3_backward(int n, int k, const double *w, const double *Z, int ldz, const 
                  void *stream);
 
 /*
+ * mr3_backward_solve -- the gradient of mr3_backward for any number k of eigenpairs (a
+ * subset included), with the eigenvector part computed one eigenpair at a time in O(n)
+ * work each instead of by two dense n x n x n products.  Since dz_k = -(T - lambda_k I)^+
+ * dT z_k, the eigenvector part of Tbar is -sum_k w_k z_k^T with w_k = (T - lambda_k I)^+ G_k,
+ * solved by tridiagonal Gaussian elimination with partial pivoting and projected off z_k
+ * (backward stable: the near-singular direction carries only rounding).  Eigenvalues
+ * closer than 1e-6 ||T|| to each
+ * other (up to 64 in a row) form a group: their components are projected out of the solve
+ * and their pairs use the regularised dense formula of mr3_backward.  With a subset, the
+ * result is exact for a loss of the computed eigenpairs as long as no eigenvalue outside
+ * the computed range lies within 1e-6 ||T|| of a computed one.
+ *
+ *  n (1), k (2) 0 <= k <= n;  d (3), e (4) device: T's diagonal (n) and off-diagonal (n-1);
+ *  w (5) device, k ascending eigenvalues;  Z (6) device n x k, ldz (7) >= max(1, n);
+ *  gw (8) device k doubles or NULL;  gZ (9) device n x k or NULL, ldgz (10);
+ *  dd (11) device out n;  de (12) device out n-1;  opts (13) may be NULL;  stream (14).
+ *  Device workspace: 4 n k + O(n) doubles from the library's pool.  Synchronises the
+ *  stream before returning.  Returns 0, -i for an invalid argument i, MR3_EOOM, MR3_ECUDA.
+ */
+int mr3_backward_solve(int n, int k, const double *d, const double *e, const double *w,
+                       const double *Z, int ldz, const double *gw, const double *gZ, int ldgz,
+                       double *dd, double *de, const mr3_opts *opts, void *stream);
+
+/*
  * mr3_stemr_static -- mr3_stemr for one matrix of order n <= MR3_STATIC_MAX_N, with all
  * device workspace inside a fixed array of MR3_STATIC_SCRATCH_BYTES that the library
  * holds on each device: the call allocates no device memory.  The thesis has no

@@ -11,6 +11,7 @@ Entry points (same names as the C ABI):
   stemr_batched(n_off, d, e, ...) -> (m, w, Z, z_off, info)
   stemr_batched_host(n_off, d, e, ...) -> (m, w, Z, z_off, info)  host arrays in and out
   backward(w, Z, gw, gZ)       -> (dbar, ebar)
+  backward_solve(d, e, w, Z, gw, gZ) -> (dbar, ebar)   any k (subsets), O(n) per eigenpair
   eigh_tridiagonal(d, e)       -> (w, Z) differentiable (torch.autograd.Function)
 """
 from __future__ import annotations
@@ -86,6 +87,9 @@ def lib():
             L.mr3_backward.argtypes = [c_int, c_int, dp, dp, c_int, dp, dp, c_int, dp, dp,
                                        ctypes.POINTER(Opts), vp]
             L.mr3_backward.restype = c_int
+            L.mr3_backward_solve.argtypes = [c_int, c_int, dp, dp, dp, dp, c_int, dp, dp, c_int,
+                                             dp, dp, ctypes.POINTER(Opts), vp]
+            L.mr3_backward_solve.restype = c_int
             L.mr3_strerror.argtypes = [c_int]
             L.mr3_strerror.restype = ctypes.c_char_p
             L.mr3_version.argtypes = []
@@ -348,6 +352,30 @@ def backward(w, Z, gw=None, gZ=None, opts=None, stream=None):
                             ctypes.c_void_p(gzp), ldgz, ctypes.c_void_p(dd.data_ptr()),
                             ctypes.c_void_p(de.data_ptr()), ctypes.byref(o), _stream_ptr(stream))
     _check(rc, "mr3_backward", allow_status=False)
+    return dd[:n], de[: max(n - 1, 0)]
+
+
+def backward_solve(d, e, w, Z, gw=None, gZ=None, opts=None, stream=None):
+    """mr3_backward_solve: (dbar, ebar) for any number of eigenpairs (w (k,), Z (n, k) with
+    column-major storage) of tridiag(e, d, e), the eigenvector part one eigenpair at a time."""
+    torch = _torch()
+    n, k = int(Z.shape[0]), int(Z.shape[1])
+    assert Z.stride(0) == 1 or k <= 1
+    ldz = Z.stride(1) if k > 1 else max(n, 1)
+    dd = torch.empty(max(n, 1), dtype=torch.float64, device=Z.device)
+    de = torch.empty(max(n - 1, 1), dtype=torch.float64, device=Z.device)
+    gzp, ldgz = 0, max(n, 1)
+    if gZ is not None:
+        gZc = gZ if (gZ.stride(0) == 1) else gZ.t().contiguous().t()
+        gzp, ldgz = gZc.data_ptr(), (gZc.stride(1) if k > 1 else max(n, 1))
+    o = opts if opts is not None else make_opts()
+    rc = lib().mr3_backward_solve(n, k, ctypes.c_void_p(d.data_ptr()),
+                                  ctypes.c_void_p(e.data_ptr() if n > 1 else 0),
+                                  ctypes.c_void_p(w.data_ptr()), ctypes.c_void_p(Z.data_ptr()), ldz,
+                                  ctypes.c_void_p(gw.data_ptr() if gw is not None else 0),
+                                  ctypes.c_void_p(gzp), ldgz, ctypes.c_void_p(dd.data_ptr()),
+                                  ctypes.c_void_p(de.data_ptr()), ctypes.byref(o), _stream_ptr(stream))
+    _check(rc, "mr3_backward_solve", allow_status=False)
     return dd[:n], de[: max(n - 1, 0)]
 
 

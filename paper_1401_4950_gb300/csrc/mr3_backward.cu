@@ -97,6 +97,50 @@ __global__ void k_apply_F(int n, const double *__restrict__ w, double delta, dou
     C[idx] = C[idx] * (D / (D * D + delta * delta));
 }
 
+// ||T|| = max(|lambda_1|, |lambda_n|) of T itself (the norm the regularisation delta of
+// mr3_backward is relative to), one warp: lanes 0-15 and 16-31 bracket lambda_1 and
+// lambda_n by 16-point multisection from the Gershgorin interval with binary64 Sturm
+// counts on T (App. B, NegCount on T; a pivot below pivmin counts as -pivmin).
+__device__ int sturm_T(int n, const double *d, const double *e, double x, double pivmin) {
+    int cnt = 0;
+    double q = d[0] - x;
+    for (int i = 0;; ++i) {
+        if (fabs(q) < pivmin) q = -pivmin;
+        cnt += q < 0.0;
+        if (i == n - 1) break;
+        q = (d[i + 1] - x) - (e[i] * e[i]) / q;
+    }
+    return cnt;
+}
+
+__global__ void k_tnorm(int n, const double *__restrict__ d, const double *__restrict__ e,
+                        double *out) {
+    const int lane = threadIdx.x & 31, half = lane >> 4, kk = lane & 15;
+    double gl = INFINITY, gu = -INFINITY, emax = 0.0;
+    for (int j = 0; j < n; ++j) {
+        const double r = (j > 0 ? fabs(e[j - 1]) : 0.0) + (j < n - 1 ? fabs(e[j]) : 0.0);
+        gl = fmin(gl, d[j] - r);
+        gu = fmax(gu, d[j] + r);
+        if (j < n - 1) emax = fmax(emax, e[j] * e[j]);
+    }
+    const double pivmin = kSafmin * fmax(1.0, emax);
+    const int target = half ? n : 1; // the count reaches target just above the eigenvalue
+    double L = gl, H = gu;
+    for (int sweep = 0; sweep < 16; ++sweep) {
+        const double x = L + (kk + 1) * ((H - L) / 17.0);
+        const unsigned bal = __ballot_sync(0xffffffffu, sturm_T(n, d, e, x, pivmin) < target);
+        const unsigned hm = (bal >> (16 * half)) & 0xffffu;
+        const int t = __popc(hm);
+        const double xl = __shfl_sync(0xffffffffu, x, 16 * half + (t > 0 ? t - 1 : 0));
+        const double xh = __shfl_sync(0xffffffffu, x, 16 * half + (t < 16 ? t : 15));
+        if (t > 0) L = xl;
+        if (t < 16) H = xh;
+    }
+    const double l1 = __shfl_sync(0xffffffffu, 0.5 * (L + H), 0);
+    const double ln = __shfl_sync(0xffffffffu, 0.5 * (L + H), 16);
+    if (lane == 0) *out = fmax(fabs(l1), fabs(ln));
+}
+
 // ---- Ozaki splitting
 
 constexpr int kOzakiMinN = 256;   // below this the binary64 tile GEMM is as fast
@@ -465,6 +509,68 @@ extern "C" int mr3_backward(int n, int k, const double *w, const double *Z, int 
             k_gemm_f64<false><<<g, 256, 0, s>>>(n, n, n, Z, ldz, C, n, Y, n);
         }
         k_row_dots<1><<<rgrid, 256, 0, s>>>(n, n, Y, n, Z, ldz, nullptr, pd, pe);
+        k_rows_finish<<<fblk, 128, 0, s>>>(n, pd, pe, 1.0, true, dd, de);
+    }
+    return done(0);
+}
+
+extern "C" int mr3_backward_solve(int n, int k, const double *d, const double *e, const double *w,
+                                  const double *Z, int ldz, const double *gw, const double *gZ,
+                                  int ldgz, double *dd, double *de, const mr3_opts *opts,
+                                  void *stream) {
+    (void)opts;
+    if (n < 0) return -1;
+    if (k < 0 || k > n) return -2;
+    if (n > 0 && !d) return -3;
+    if (n > 1 && !e) return -4;
+    if (k > 0 && !w) return -5;
+    if (k > 0 && !Z) return -6;
+    if (ldz < std::max(1, n)) return -7;
+    if (gZ && ldgz < std::max(1, n)) return -10;
+    if (n > 0 && !dd) return -11;
+    if (n > 1 && !de) return -12;
+    if (n == 0) return 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    double *part = nullptr, *Y = nullptr, *scr = nullptr;
+    const bool vec = gZ && n > 1 && k > 0;
+    auto done = [&](int code) {
+        if (part) cudaFreeAsync(part, s);
+        if (Y) cudaFreeAsync(Y, s);
+        if (scr) cudaFreeAsync(scr, s);
+        if (code == 0 && cudaStreamSynchronize(s) != cudaSuccess) { cudaGetLastError(); return (int)MR3_ECUDA; }
+        return code;
+    };
+    if (lib_malloc_async((void **)&part, sizeof(double) * 2 * kRowChunks * (size_t)n, s) != cudaSuccess ||
+        (vec && lib_malloc_async((void **)&Y, sizeof(double) * (size_t)n * k, s) != cudaSuccess) ||
+        (vec && lib_malloc_async((void **)&scr, sizeof(double) * 3 * (size_t)n * k, s) != cudaSuccess)) {
+        cudaGetLastError();
+        return done(MR3_EOOM);
+    }
+    double *pd = part, *pe = part + (size_t)kRowChunks * n;
+    const dim3 rgrid((n + 31) / 32, kRowChunks);
+    const unsigned fblk = (unsigned)((n + 127) / 128);
+    if (gw && k > 0) {
+        k_row_dots<0><<<rgrid, 256, 0, s>>>(n, k, nullptr, 1, Z, ldz, gw, pd, pe);
+        k_rows_finish<<<fblk, 128, 0, s>>>(n, pd, pe, 2.0, false, dd, de);
+    } else {
+        if (cudaMemsetAsync(dd, 0, sizeof(double) * n, s) != cudaSuccess ||
+            (n > 1 && cudaMemsetAsync(de, 0, sizeof(double) * (n - 1), s) != cudaSuccess))
+            return done(MR3_ECUDA);
+    }
+    if (vec) {
+        // ||T|| = max |lambda| of T (16 sweeps of 16-point multisection: 2^-64 of the
+        // Gershgorin width, far below what delta needs)
+        double hd[1];
+        int rc = 0;
+        double *gmax = nullptr;
+        if (lib_malloc_async((void **)&gmax, sizeof(double), s) != cudaSuccess) { cudaGetLastError(); return done(MR3_EOOM); }
+        k_tnorm<<<1, 32, 0, s>>>(n, d, e, gmax);
+        if (read_back(hd, gmax, sizeof(double), s) != cudaSuccess) rc = MR3_ECUDA;
+        cudaFreeAsync(gmax, s);
+        if (rc) return done(rc);
+        const double tnorm = hd[0] > 0.0 ? hd[0] : 1.0;
+        launch_adjoint(n, k, d, e, w, Z, ldz, gZ, ldgz, tnorm, scr, Y, s);
+        k_row_dots<1><<<rgrid, 256, 0, s>>>(n, k, Y, n, Z, ldz, nullptr, pd, pe);
         k_rows_finish<<<fblk, 128, 0, s>>>(n, pd, pe, 1.0, true, dd, de);
     }
     return done(0);

@@ -118,6 +118,11 @@ cudaError_t read_back(void *dst, const void *src, size_t bytes, cudaStream_t s);
 int tc_gemm_bf16(int M, int N, int K, int k0, int k1, const unsigned short *A, int lda,
                  const unsigned short *B, int ldb, float *C, int ldc, int *err, cudaStream_t s);
 cudaError_t preload_tc_gemm();
+// Eigenvector part of the backward pass one eigenpair at a time (mr3_adjoint.cu): column c
+// of Y (n x k, ld n) such that Y Z^T is the eigenvector part of Tbar; scratch 3 n k doubles.
+void launch_adjoint(int n, int k, const double *d, const double *e, const double *w,
+                    const double *Z, int ldz, const double *G, int ldg, double tnorm,
+                    double *scratch, double *Y, cudaStream_t s);
 cudaError_t preload_prologue();
 cudaError_t preload_levels();
 cudaError_t preload_rqi();
