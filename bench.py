@@ -54,7 +54,9 @@ ORACLE_SAMPLE = 256
 # of one step and divided by their number), valid only while the kernel source it was
 # taken on is unchanged: source file, its sha256 prefix at capture time, and the summary
 # under profiles/ that holds the counters.
-TRAFFIC = {}
+TRAFFIC = {"k_rqi": {"bytes_per_launch": 3.187e9,
+                     "source": "paper_1401_4950_gb300/csrc/mr3_rqi.cu", "sha": "d208cfc403e20429",
+                     "profile": "profiles/k_rqi_traffic_step_n8192.md"}}
 
 CONFIGS = {
     "c1": {"workload": "plain MRRR, n=1000 uniform(-1,1) d and e, all eigenpairs, FP64",
@@ -542,8 +544,34 @@ def backward_leg(args):
         tb.append(c.elapsed_time(dd_))
     wc = w.cpu().numpy()
     fm, bm = statistics.median(tf), statistics.median(tb)
+    # the per-eigenpair adjoint (mr3_backward_solve) on the same problem, and on the middle
+    # 20% of the eigenpairs (a subset, which the dense path does not take)
+    ts = []
+    for _ in range(reps):
+        a, b = _events()
+        a.record()
+        mr3.backward_solve(dt, et, w, Z, g, G)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    il, iu = 2 * n // 5 + 1, 3 * n // 5
+    ws, Zs, _ = mr3.stemr(dt, et, rng="I", il=il, iu=iu)
+    gs, Gs = g[il - 1:iu].contiguous(), G[:, il - 1:iu]
+    tsub = []
+    for _ in range(reps):
+        a, b = _events()
+        a.record()
+        mr3.backward_solve(dt, et, ws, Zs, gs, Gs)
+        b.record()
+        torch.cuda.synchronize()
+        tsub.append(a.elapsed_time(b))
+    sm, ssub = statistics.median(ts), statistics.median(tsub)
     return {"metric": "backward / forward time (n=%d, all eigenpairs, FP64)" % n,
             "value": bm / fm, "unit": "ratio", "forward_ms": fm, "backward_ms": bm,
+            "backward_path": "dense: two n^3 products as exact sums of bf16 slice products "
+                             "on the library's tcgen05 kernel",
+            "solve_backward_ms": sm, "solve_over_forward": sm / fm,
+            "subset": {"il": il, "iu": iu, "solve_backward_ms": ssub},
             "min_eigenvalue_gap": float(np.min(np.diff(wc))) if n > 1 else None}
 
 
