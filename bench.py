@@ -54,9 +54,10 @@ ORACLE_SAMPLE = 256
 # of one step and divided by their number), valid only while the kernel source it was
 # taken on is unchanged: source file, its sha256 prefix at capture time, and the summary
 # under profiles/ that holds the counters.
+# The capture's RQI team size is part of its validity (0: the library's own rule).
 TRAFFIC = {"k_rqi": {"bytes_per_launch": 3.187e9,
                      "source": "paper_1401_4950_gb300/csrc/mr3_rqi.cu", "sha": "d208cfc403e20429",
-                     "profile": "profiles/k_rqi_traffic_step_n8192.md"}}
+                     "profile": "profiles/k_rqi_traffic_step_n8192.md", "rqi_team": 0}}
 
 CONFIGS = {
     "c1": {"workload": "plain MRRR, n=1000 uniform(-1,1) d and e, all eigenpairs, FP64",
@@ -256,13 +257,26 @@ def _source_sha(path):
     return hashlib.sha256(open(os.path.join(ROOT, path), "rb").read()).hexdigest()[:16]
 
 
-def traffic_for(kernel):
+def traffic_for(kernel, rqi_team=0):
     """DRAM bytes per launch of `kernel` from its capture, or None when the kernel's source
-    changed after the capture (or no capture exists)."""
+    changed after the capture, the step runs another RQI team size than the capture did,
+    or no capture exists."""
     t = TRAFFIC.get(kernel)
     if not t or _source_sha(t["source"]) != t["sha"]:
         return None
+    if kernel == "k_rqi" and t.get("rqi_team", 0) != rqi_team:
+        return None
     return t["bytes_per_launch"]
+
+
+def autotuned(n_off, d, e, args, tree_opts=None):
+    """The launch shape for this batch: tuned now (untimed, before the warm-up) unless
+    --no-autotune, else the library's rules.  Returns (rqi_team, bisect_warps, record)."""
+    if args.no_autotune or args.prec == "dd":
+        return 0, 0, None
+    from paper_1401_4950_gb300 import autotune
+    rec = autotune.tune(n_off, d, e, reps=2, warmup=1, tree_opts=tree_opts)
+    return rec["rqi_team"], rec["bisect_warps"], rec
 
 
 # ------------------------------------------------------------------ GPU legs
@@ -281,7 +295,6 @@ def run_gpu(args, cfg, rank, world):
     dev_mats = [(k, torch.tensor(d, device=dev), torch.tensor(e, device=dev)) for k, d, e in mats]
     units_per_step = sum(len(d) for _, d, _ in mats)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    opts = mr3.make_opts(profile=1, prec=mr3.DD if args.prec == "dd" else mr3.FP64)
     stream = torch.cuda.current_stream()
     # the step's matrices packed for one mr3_stemr_batched call (d and e with the same
     # offsets, the last e slot of each matrix unused)
@@ -291,6 +304,10 @@ def run_gpu(args, cfg, rank, world):
     dcat_h = np.concatenate([np.asarray(d, dtype=np.float64) for _, d, _ in mats])
     ecat_h = np.concatenate([np.r_[np.asarray(e, dtype=np.float64), 0.0] for _, _, e in mats])
     dcat, ecat = torch.tensor(dcat_h, device=dev), torch.tensor(ecat_h, device=dev)
+    tree_flags = {"abs_split": -1 if args.relative_only else 0, "erep": int(args.erep)}
+    team, bwarps, tuned = autotuned(n_off, dcat, ecat, args, tree_flags)
+    opts = mr3.make_opts(profile=1, prec=mr3.DD if args.prec == "dd" else mr3.FP64,
+                         rqi_team=team, bisect_warps=bwarps, **tree_flags)
 
     def step():
         """One step; returns the solver statistics and each matrix's (w, Z) on the device."""
@@ -374,7 +391,7 @@ def run_gpu(args, cfg, rank, world):
     achieved_w = (fpu_w * units / 1e12) / (ms / 1e3) if ms > 0 else 0.0
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": traffic_for(kname),
+                "traffic": traffic_for(kname, team),
                 "frac_divide_weighted": achieved_w / FP64_PEAK_TFLOPS,
                 "peak_source": "FP64 pipe: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz, from unit "
                                "counts and the maximum clock (MEASURED_PEAKS.json has no FP64 "
@@ -396,7 +413,7 @@ def run_gpu(args, cfg, rank, world):
     zlen = int(sum(n * n for n in sizes))
     wh = torch.empty(int(n_off[-1]), dtype=torch.float64).pin_memory()
     Zh = torch.empty(zlen, dtype=torch.float64).pin_memory()
-    e2e_opts = mr3.make_opts(prec=opts.prec)
+    e2e_opts = mr3.make_opts(prec=opts.prec, rqi_team=team, bisect_warps=bwarps, **tree_flags)
 
     def e2e_step():
         if args.solver == "single":
@@ -440,7 +457,10 @@ def run_gpu(args, cfg, rank, world):
                        "(256 MiB device write outside the per-step events)",
                        "parallelism": "replicas, one set of matrices per GPU",
                        "solver": args.solver,
-                       "tree": "double-double (Ch. 5)" if args.prec == "dd" else "binary64"},
+                       "tree": "double-double (Ch. 5)" if args.prec == "dd" else "binary64",
+                       "launch_shape": {"rqi_team": team, "bisect_warps": bwarps,
+                                        "autotune": tuned},
+                       "tree_options": tree_flags},
             "accuracy": accuracy,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(agg["kernel_launches"].sum()),
@@ -477,7 +497,8 @@ def batched_leg(args):
     sizes, n_off, d, e = tm.batched_random(nb)
     dt = torch.tensor(d, device=dev)
     et = torch.tensor(e, device=dev)
-    opts = mr3.make_opts(profile=1)
+    team, bwarps, tuned = autotuned(n_off, dt, et, args)
+    opts = mr3.make_opts(profile=1, rqi_team=team, bisect_warps=bwarps)
     for _ in range(2):
         mr3.stemr_batched(n_off, dt, et, opts=opts)
     torch.cuda.synchronize()
@@ -491,14 +512,16 @@ def batched_leg(args):
         torch.cuda.synchronize()
         tb.append(a.elapsed_time(b))
         del w, Z
+    # the per-matrix loop runs with the library's own launch-shape rules
+    popts = mr3.make_opts()
     views = [(dt[n_off[b]:n_off[b + 1]], et[n_off[b]:n_off[b + 1]]) for b in range(nb)]
     for b in range(min(nb, 8)):
-        mr3.stemr(*views[b])
+        mr3.stemr(*views[b], opts=popts)
     torch.cuda.synchronize()
     a, b_ = _events()
     a.record()
     for b in range(nb):
-        mr3.stemr(*views[b])
+        mr3.stemr(*views[b], opts=popts)
     b_.record()
     torch.cuda.synchronize()
     tp = a.elapsed_time(b_)
@@ -509,6 +532,7 @@ def batched_leg(args):
             "per_matrix_ms": tp, "eigenpairs": int(n_off[-1]),
             "kernel_ms": [round(x, 3) for x in info["kernel_ms"]], "dmax": info["dmax"],
             "nclusters": info["nclusters"], "rqi_iters": info["rqi_iters"],
+            "launch_shape": {"rqi_team": team, "bisect_warps": bwarps, "autotune": tuned},
             "config": "sizes seed 401; matrix b: d seed 402+2b, e seed 403+2b"}
 
 
@@ -669,6 +693,14 @@ def main():
                          "call each")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "dd"],
                     help="representation tree in binary64 or double-double (Ch. 5)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's launch-shape rules instead of tuning the RQI "
+                         "team size and bisection warps per SM on the workload first")
+    ap.add_argument("--relative-only", action="store_true",
+                    help="classify by relative gaps only (opts.abs_split = -1; the default "
+                         "amends the root classification by absolute gaps)")
+    ap.add_argument("--erep", action="store_true",
+                    help="binary64 child representations as e-representations (opts.erep)")
     ap.add_argument("--leg", default=None,
                     choices=["batched", "backward", "subset", "left_subsets"],
                     help="print only one of the extra legs as its own JSON line")

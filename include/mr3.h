@@ -76,7 +76,24 @@ typedef struct {
     int max_depth;             /* cap on the representation-tree depth [64]                  */
     int profile;               /* nonzero: time each kernel group with CUDA events on the
                                   call's stream and report it in mr3_info.kernel_ms [0]        */
-    int reserved[5];
+    int rqi_team;              /* lanes per singleton in the RQI: 0 = auto (2 for many
+                                  singletons, else 8), 2 or 8 to force one [0]               */
+    int bisect_warps;          /* bisection lanes per eigenvalue are chosen to keep about this
+                                  many warps per SM in flight: 0 = 48, else 1..64 (tpe > 0
+                                  overrides) [0]                                              */
+    int abs_split;             /* the root's classification also separates neighbours whose
+                                  absolute gap is at least the block's average gap
+                                  spdiam / (n_b - 1) (the relative criterion amended by
+                                  absolute gaps, Sec. 3.2.3, Sec. 4.2.1); the pieces cut out
+                                  of a relative cluster get their own representations.
+                                  0 or positive = on, negative = off (relative gaps only).
+                                  mr3_stemr_static never applies it [0: on]                  */
+    int erep;                  /* nonzero: binary64 child representations are kept as
+                                  e-representations (d, beta): the off-diagonal entries are
+                                  shared with the root instead of recomputed as d+ l+ (Ch. 3,
+                                  representation forms; Ch. 5).  The double-double tree always
+                                  works this way [0]                                         */
+    int reserved[1];
 } mr3_opts;
 
 /* Fault injection (tests of the safeguards; nothing here faults a GPU). */

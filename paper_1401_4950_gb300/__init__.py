@@ -35,7 +35,9 @@ class Opts(ctypes.Structure):
                 ("seed", ctypes.c_ulonglong), ("max_rqi", ctypes.c_int),
                 ("max_shift_tries", ctypes.c_int), ("fault_mask", ctypes.c_uint),
                 ("tpe", ctypes.c_int), ("max_depth", ctypes.c_int),
-                ("profile", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("profile", ctypes.c_int), ("rqi_team", ctypes.c_int),
+                ("bisect_warps", ctypes.c_int), ("abs_split", ctypes.c_int),
+                ("erep", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 class Info(ctypes.Structure):
@@ -112,11 +114,14 @@ KERNEL_GROUPS = ("prologue", "root", "bisect_root", "classify", "rqi", "shift", 
 
 
 def make_opts(prec=FP64, gaptol=0.0, seed=0, max_rqi=0, max_shift_tries=0, fault_mask=0,
-              tpe=0, max_depth=0, profile=0) -> Opts:
+              tpe=0, max_depth=0, profile=0, rqi_team=0, bisect_warps=0, abs_split=0,
+              erep=0) -> Opts:
     o = Opts()
     o.prec, o.gaptol, o.seed, o.max_rqi = prec, gaptol, seed, max_rqi
     o.max_shift_tries, o.fault_mask, o.tpe, o.max_depth = max_shift_tries, fault_mask, tpe, max_depth
-    o.profile = profile
+    o.profile, o.rqi_team, o.bisect_warps = profile, rqi_team, bisect_warps
+    # abs_split: 0 (default) or positive = absolute-gap amendment on, negative = off
+    o.abs_split, o.erep = int(abs_split), int(bool(erep))
     return o
 
 

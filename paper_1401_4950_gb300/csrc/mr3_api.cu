@@ -12,6 +12,11 @@
 
 namespace mr3 {
 
+// Bisection lanes per eigenvalue keep about this many warps per SM in flight by default.
+#ifndef MR3_BISECT_WARPS_PER_SM
+#define MR3_BISECT_WARPS_PER_SM 48
+#endif
+
 namespace {
 
 struct Opts {
@@ -24,6 +29,10 @@ struct Opts {
     int tpe;
     int max_depth;
     int profile;
+    int rqi_team;
+    int bisect_warps;
+    int abs_split;
+    int erep;
 };
 
 Opts resolve(const mr3_opts *o) {
@@ -37,21 +46,23 @@ Opts resolve(const mr3_opts *o) {
     r.tpe = o ? o->tpe : 0;
     r.max_depth = (o && o->max_depth > 0) ? o->max_depth : 64;
     r.profile = o ? o->profile : 0;
+    r.rqi_team = (o && (o->rqi_team == 2 || o->rqi_team == 8)) ? o->rqi_team : 0;
+    r.bisect_warps = (o && o->bisect_warps > 0 && o->bisect_warps <= 64) ? o->bisect_warps
+                                                                         : MR3_BISECT_WARPS_PER_SM;
+    r.abs_split = (o && o->abs_split < 0) ? 0 : 1;
+    r.erep = (o && o->erep) ? 1 : 0;
     return r;
 }
 
 // Lanes per eigenvalue for the multisection: enough lanes in flight to keep the SMs busy
 // (about MR3_BISECT_WARPS_PER_SM warps per SM on 152 SMs), at most 32; opts->tpe overrides.
-#ifndef MR3_BISECT_WARPS_PER_SM
-#define MR3_BISECT_WARPS_PER_SM 48
-#endif
 int lanes_for(long long nactive, const Opts &o) {
     if (o.tpe > 0) {
         int L = 1;
         while (L * 2 <= o.tpe && L < 32) L *= 2;
         return L;
     }
-    const long long target = 152ll * 32 * MR3_BISECT_WARPS_PER_SM;
+    const long long target = 152ll * 32 * o.bisect_warps;
     int L = 1;
     while (L < 32 && (long long)(2 * L) * nactive <= target) L *= 2;
     return L;
@@ -323,8 +334,10 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
     double *gapl = ws.get<double>(ncols);
     double *gapr = ws.get<double>(ncols);
     SingleItem *singles = ws.get<SingleItem>(ncols);
-    ClusterItem *clusters = ws.get<ClusterItem>(ncols / 2 + 1);
-    long long *crep = ws.get<long long>(ncols / 2 + 1);
+    // clusters have two members or more, except the root's pieces of the absolute-gap split
+    const long long max_clusters = o.abs_split ? ncols + 1 : ncols / 2 + 1;
+    ClusterItem *clusters = ws.get<ClusterItem>(max_clusters);
+    long long *crep = ws.get<long long>(max_clusters);
     LevelCounters *ctr = ws.get<LevelCounters>(1);
     int *work = ws.get<int>(1);
     CKW(ws);
@@ -390,7 +403,7 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
     const long long scratch_cap_bytes = 8ll << 30;
     int status = 0;
     auto run_singles = [&](int level, const LevelCounters &hc) -> int {
-        const int team = dd ? 0 : rqi_team(hc.nsingle, nmat);
+        const int team = dd ? 0 : (o.rqi_team ? o.rqi_team : rqi_team(hc.nsingle, nmat));
         long long slots = dd ? rqi_dd_threads(hc.nsingle, nmax, 2 * scratch_cap_bytes)
                              : rqi_slots(hc.nsingle, nmax, scratch_cap_bytes, team);
         const size_t per_slot = dd ? (size_t)4 * nmax : (size_t)rqi_scratch_per_index(team) * nmax;
@@ -436,7 +449,8 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
         if (rqi_done[level & 1]) { cudaStreamWaitEvent(s, rqi_done[level & 1], 0); rqi_done[level & 1] = nullptr; }
         CK(cudaMemsetAsync(ctr, 0, sizeof(LevelCounters), s));
         tk = prof.begin();
-        launch_classify(ncur, cur_nodes, blks, lo, hi, o.gaptol, gapl, gapr, singles2[level & 1],
+        launch_classify(ncur, cur_nodes, blks, lo, hi, o.gaptol, o.abs_split ? 1.0 : 0.0, gapl,
+                        gapr, singles2[level & 1],
                         clusters, crep, cnode, ctr, dinfo, s);
         prof.end(tk, 3, 1);
         LevelCounters hc;
@@ -461,7 +475,7 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
         launch_refine_ends(hc.ncluster, clusters, cur_nodes, blks, cur_pool, jloc, lo, hi, tri, dinfo, s);
         launch_shift(hc.ncluster, clusters, crep, cur_nodes, blks, cur_pool, next_pool,
                      next_nodes, tau, cnode, next_active, jloc, lo, hi, o.max_tries, o.fault_mask,
-                     tri, shift_ws, dinfo, s);
+                     o.erep, tri, shift_ws, dinfo, s);
         if (dd)
             launch_shift_dd(hc.ncluster, clusters, crep, cur_nodes, blks, cur_pool, cur_lo, next_pool,
                             next_lo, next_nodes, tau, dinfo, s);
@@ -492,7 +506,7 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
             const int lv = level + 1;
             if (rqi_done[lv & 1]) { cudaStreamWaitEvent(s, rqi_done[lv & 1], 0); rqi_done[lv & 1] = nullptr; }
             CK(cudaMemsetAsync(ctr, 0, sizeof(LevelCounters), s));
-            launch_classify(ncur, cur_nodes, blks, lo, hi, -1e308, gapl, gapr, singles2[lv & 1],
+            launch_classify(ncur, cur_nodes, blks, lo, hi, -1e308, 0.0, gapl, gapr, singles2[lv & 1],
                             clusters, crep, cnode, ctr, dinfo, s);
             CK(read_back(&hc, ctr, sizeof(hc), s));
             if (hc.nsingle > 0) {

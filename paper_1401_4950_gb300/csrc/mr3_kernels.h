@@ -49,8 +49,12 @@ void launch_bisect(int ngroups, const int *list, int L, int mtotal, const int *c
 // Shared grid of Sturm counts giving the starting intervals of the root level.
 void launch_grid(int nblk, const BlkDesc *blks, const Node *nodes, const double *pool, int *grid,
                  double *lo, double *hi, int max_m, DevInfo *info, cudaStream_t s);
+// absfac > 0: at the root (depth 0) also separate j, j+1 when their absolute gap is at least
+// absfac times the block's average gap spdiam / (n_b - 1) (the amendment of the relative
+// criterion by absolute gaps, Sec. 3.2.3 and Sec. 4.2.1); the pieces this extra split cuts
+// out of a relative cluster stay clusters, however small.
 void launch_classify(int nnode, const Node *nodes, const BlkDesc *blks, const double *lo,
-                     const double *hi, double gaptol, double *gapl, double *gapr,
+                     const double *hi, double gaptol, double absfac, double *gapl, double *gapr,
                      SingleItem *singles, ClusterItem *clusters, long long *cluster_rep,
                      int *cnode, LevelCounters *ctr, DevInfo *info, cudaStream_t s);
 // Refine the two extreme eigenvalues of every cluster (Alg. "Shifting the spectrum", first step).
@@ -64,7 +68,7 @@ void launch_shift(int ncluster, const ClusterItem *clusters, const long long *cl
                   const Node *nodes, const BlkDesc *blks, const double *pool, double *childpool,
                   Node *child_nodes, double *child_tau, int *cnode, int *active_list,
                   const int *jloc, double *lo, double *hi, int max_tries, unsigned fault_mask,
-                  double2 *tri, void *ws, DevInfo *info, cudaStream_t s);
+                  int erep, double2 *tri, void *ws, DevInfo *info, cudaStream_t s);
 // Stream-ordered allocation from the library's memory pool of the current device (one
 // pool per device whose release threshold keeps freed memory for later calls); free with
 // cudaFreeAsync.

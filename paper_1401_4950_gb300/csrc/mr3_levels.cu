@@ -286,13 +286,23 @@ void launch_grid(int nblk, const BlkDesc *blks, const Node *nodes, const double 
 // One warp per node.  Consecutive eigenvalues j, j+1 of the node are separated when
 //   reldist(j, j+1) = (lo_{j+1} - hi_j) / max(|lo_j|, |hi_j|, |lo_{j+1}|, |hi_{j+1}|) >= gaptol
 // (Sec. 3.2.3, Classification); gaptol == kGaptolAuto selects auto_gaptol(n_b) for the
-// node's block.  The boundary flags of 32 columns at a time are combined
-// with a ballot; groups of one column become singletons, longer groups clusters.  Items
-// are appended with one atomic per warp and kind.  gapl/gapr receive the absolute gaps
-// of every column to its neighbours (used by the RQI acceptance test).
+// node's block.  With absfac > 0, a root node also separates j, j+1 when
+//   mid_{j+1} - mid_j >= absfac * spdiam / (n_b - 1),   mid = (lo + hi) / 2,
+// i.e. when their absolute gap reaches absfac times the average gap of the block (the
+// absolute-gap amendment, Sec. 3.2.3 and Sec. 4.2.1).  The gap is taken between the
+// midpoints: at classification accuracy the intervals' widths (rtol |lambda|) are a
+// sizeable part of the average gap once n_b is in the thousands, and the bound gap
+// lo_{j+1} - hi_j would split less the larger the matrix.  A piece that such a split cuts out
+// of a relative cluster is a cluster even when it has one member: its relative gap in the
+// root representation is below gaptol, so its vector needs a representation shifted close
+// to it.  The boundary flags of 32 columns at a time are combined with a ballot; groups
+// of one column bounded by relative gaps on both sides become singletons, the other groups
+// clusters.  Items are appended with one atomic per warp and kind.  gapl/gapr receive the
+// absolute gaps of every column to its neighbours (used by the RQI acceptance test).
 __global__ void k_classify(int nnode, const Node *__restrict__ nodes, const BlkDesc *__restrict__ blks,
                            const double *__restrict__ lo, const double *__restrict__ hi,
-                           double gaptol, double *gapl, double *gapr, SingleItem *singles,
+                           double gaptol, double absfac, double *gapl, double *gapr,
+                           SingleItem *singles,
                            ClusterItem *clusters, long long *cluster_rep, int *cnode,
                            LevelCounters *ctr, DevInfo *info) {
     const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -302,13 +312,16 @@ __global__ void k_classify(int nnode, const Node *__restrict__ nodes, const BlkD
     if (N.c1 < N.c0) return;
     const int nb = blks[N.blk].n;
     const double gt = (gaptol == kGaptolAuto) ? auto_gaptol(nb) : gaptol;
+    const double absgap = (absfac > 0.0 && N.depth == 0 && nb > 1)
+                              ? absfac * blks[N.blk].spdiam / (double)(nb - 1) : INFINITY;
     int gstart = N.c0;
+    bool gstart_rel = true; // the boundary before gstart is a relative one (or the node's start)
     int maxsize = 0, nclus = 0;
     for (int base = N.c0; base <= N.c1; base += 32) {
         const int c = base + lane;
         const bool valid = c <= N.c1;
         double l = 0.0, h = 0.0, ln = 0.0, hn = 0.0;
-        bool end = false;
+        bool end = false, end_rel = false;
         if (valid) {
             l = lo[c];
             h = hi[c];
@@ -317,9 +330,10 @@ __global__ void k_classify(int nnode, const Node *__restrict__ nodes, const BlkD
                 hn = hi[c + 1];
                 const double den = fmax(fmax(fabs(l), fabs(h)), fmax(fabs(ln), fabs(hn)));
                 const double rd = (ln - h) / den;
-                end = !(rd < gt); // also separates on NaN (never join on bad data)
+                end_rel = !(rd < gt); // also separates on NaN (never join on bad data)
+                end = end_rel || (0.5 * (ln + hn) - 0.5 * (l + h) >= absgap);
             } else {
-                end = true;
+                end = end_rel = true;
             }
             const double left = (c > N.c0) ? hi[c - 1] : N.lnb;
             const double right = (c < N.c1) ? ln : N.rnb;
@@ -328,14 +342,20 @@ __global__ void k_classify(int nnode, const Node *__restrict__ nodes, const BlkD
             cnode[c] = -1;
         }
         const unsigned mask = __ballot_sync(FULL_MASK, end);
+        const unsigned mrel = __ballot_sync(FULL_MASK, end_rel);
         int gs = gstart;
+        bool lrel = gstart_rel;
         if (end) {
             const unsigned prev = mask & ((1u << lane) - 1u);
-            if (prev) gs = base + (31 - __clz(prev)) + 1;
+            if (prev) {
+                const int b = 31 - __clz(prev);
+                gs = base + b + 1;
+                lrel = (mrel >> b) & 1u;
+            }
         }
         const int size = end ? c - gs + 1 : 0;
-        const bool single = end && size == 1;
-        const bool clus = end && size >= 2;
+        const bool single = end && size == 1 && lrel && end_rel;
+        const bool clus = end && !single;
         const unsigned ms = __ballot_sync(FULL_MASK, single);
         const unsigned mc = __ballot_sync(FULL_MASK, clus);
         int sbase = 0, cbase = 0;
@@ -382,7 +402,11 @@ __global__ void k_classify(int nnode, const Node *__restrict__ nodes, const BlkD
             maxsize = max(maxsize, size);
             nclus++;
         }
-        if (mask) gstart = base + (31 - __clz(mask)) + 1;
+        if (mask) {
+            const int b = 31 - __clz(mask);
+            gstart = base + b + 1;
+            gstart_rel = (mrel >> b) & 1u;
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         maxsize = max(maxsize, __shfl_xor_sync(FULL_MASK, maxsize, o));
@@ -397,13 +421,13 @@ __global__ void k_classify(int nnode, const Node *__restrict__ nodes, const BlkD
 }
 
 void launch_classify(int nnode, const Node *nodes, const BlkDesc *blks, const double *lo,
-                     const double *hi, double gaptol, double *gapl, double *gapr,
+                     const double *hi, double gaptol, double absfac, double *gapl, double *gapr,
                      SingleItem *singles, ClusterItem *clusters, long long *cluster_rep,
                      int *cnode, LevelCounters *ctr, DevInfo *info, cudaStream_t s) {
     if (nnode <= 0) return;
     const int wpb = 4;
     k_classify<<<(nnode + wpb - 1) / wpb, 32 * wpb, 0, s>>>(nnode, nodes, blks, lo, hi, gaptol,
-                                                            gapl, gapr, singles, clusters,
+                                                            absfac, gapl, gapr, singles, clusters,
                                                             cluster_rep, cnode, ctr, info);
 }
 
@@ -419,7 +443,9 @@ void launch_classify(int nnode, const Node *nodes, const BlkDesc *blks, const do
 // stops at 1e-13 relative width (near the practical accuracy of its counts on the scaled
 // copy), phase 1 checks those bounds with binary64 counts, widens where they fail, and
 // continues in binary64 with fewer lanes per end (the binary64 pipe, not latency, bounds
-// it when ends are many).
+// it when ends are many).  A cluster of one member (cut out by the absolute-gap split) has
+// no inner neighbour: its one eigenvalue is refined to full accuracy by the group of its
+// left end, and the group of its right end stays idle.
 __global__ void k_refine_ends(int ncluster, const ClusterItem *__restrict__ clusters,
                               const Node *__restrict__ nodes, const BlkDesc *__restrict__ blks,
                               const double *__restrict__ pool, const int *__restrict__ jloc,
@@ -429,13 +455,14 @@ __global__ void k_refine_ends(int ncluster, const ClusterItem *__restrict__ clus
     const int lane = threadIdx.x & 31;
     const int g = tid / E, k = lane % E, gbase = lane - k;
     const unsigned gmask = (E == 32) ? 0xffffffffu : (((1u << E) - 1u) << gbase);
-    const bool active = g < 2 * ncluster;
+    bool active = g < 2 * ncluster;
     const int side = g & 1;
     int n = 1, tgt = 1, col = 0;
     Node P;
     P.dfok = 0;
     const double *pd = pool;
     double L = 0.0, H = 0.0, nb = 0.0;
+    if (active && side == 1 && clusters[g >> 1].c0 == clusters[g >> 1].c1) active = false;
     if (active) {
         const ClusterItem C = clusters[g >> 1];
         P = nodes[C.node];
@@ -445,7 +472,7 @@ __global__ void k_refine_ends(int ncluster, const ClusterItem *__restrict__ clus
         tgt = jloc[col];
         L = lo[col];
         H = hi[col];
-        nb = side ? hi[col - 1] : lo[col + 1];
+        nb = (C.c0 == C.c1) ? -INFINITY : (side ? hi[col - 1] : lo[col + 1]);
         // phase 1 resumes with the neighbour bound phase 0 tightened
         if (phase == 1) nb = carry[g].x;
     }
@@ -852,12 +879,16 @@ __global__ void k_shift_recompute(int nslots, const ClusterItem *__restrict__ cl
 //     k_shift_pick); the first t with an accepted candidate wins and is recomputed
 //     (k_shift_recompute), else the least growth overall (counted untested).
 //  3. The winner's c_i give the child: d+_i = c_i / c_{i-1}, l+_i = dl_i / d+_i,
-//     dl+_i = d+_i l+_i, dll+_i = dl+_i l+_i, converted in place by chunks of 32.
+//     dl+_i = d+_i l+_i, dll+_i = dl+_i l+_i, converted in place by chunks of 32.  With
+//     erep the child is kept as an e-representation (Ch. 3, representation forms; Ch. 5
+//     on the choice of form): its primary data are d+ and the off-diagonal entries
+//     beta_i = dl_i, which dstqds leaves unchanged, so dl+ = dl exactly (every node of the
+//     tree then carries the root's beta bit for bit) and dll+_i = beta_i (beta_i / d+_i).
 __global__ void k_shift(int ncluster, const ClusterItem *__restrict__ clusters,
                         const long long *__restrict__ cluster_rep, const Node *__restrict__ nodes,
                         const BlkDesc *__restrict__ blks, const double *__restrict__ pool,
                         double *childpool, Node *child_nodes, double *child_tau, int *cnode,
-                        int *active_list, const ShiftDecision *__restrict__ dec,
+                        int *active_list, const ShiftDecision *__restrict__ dec, int erep,
                         DevInfo *info) {
     const int ci = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -899,7 +930,7 @@ __global__ void k_shift(int ncluster, const ClusterItem *__restrict__ clusters,
             cd[i] = dp;
             if (i < n - 1) {
                 const double lp = pdl[i] / dp;
-                const double dlp = dp * lp;
+                const double dlp = erep ? pdl[i] : dp * lp;
                 dllp = dlp * lp;
                 cdl[i] = dlp;
                 cdll[i] = dllp;
@@ -949,7 +980,7 @@ void launch_shift(int ncluster, const ClusterItem *clusters, const long long *cl
                   const Node *nodes, const BlkDesc *blks, const double *pool, double *childpool,
                   Node *child_nodes, double *child_tau, int *cnode, int *active_list,
                   const int *jloc, double *lo, double *hi, int max_tries, unsigned fault_mask,
-                  double2 *tri, void *ws, DevInfo *info, cudaStream_t s) {
+                  int erep, double2 *tri, void *ws, DevInfo *info, cudaStream_t s) {
     (void)jloc;
     if (ncluster <= 0) return;
     const int NL = ladder_width(max_tries);
@@ -975,7 +1006,7 @@ void launch_shift(int ncluster, const ClusterItem *clusters, const long long *cl
         ncluster, clusters, cluster_rep, nodes, blks, pool, childpool, recomp, counts, dec, info);
     // conversion to the child representations, one warp per cluster
     k_shift<<<ncluster, 32, 0, s>>>(ncluster, clusters, cluster_rep, nodes, blks, pool, childpool,
-                                    child_nodes, child_tau, cnode, active_list, dec, info);
+                                    child_nodes, child_tau, cnode, active_list, dec, erep, info);
 }
 
 // ------------------------------------------------------------------ output order

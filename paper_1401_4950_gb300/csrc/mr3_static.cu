@@ -109,13 +109,13 @@ struct Arena {
         if ((ar).full) return MR3_ENOSCRATCH;                                            \
     } while (0)
 
-int lanes_auto(long long nactive, int tpe) {
+int lanes_auto(long long nactive, int tpe, int warps_per_sm) {
     if (tpe > 0) {
         int L = 1;
         while (L * 2 <= tpe && L < 32) L *= 2;
         return L;
     }
-    const long long target = 152ll * 32 * 48;
+    const long long target = 152ll * 32 * warps_per_sm;
     int L = 1;
     while (L < 32 && (long long)(2 * L) * nactive <= target) L *= 2;
     return L;
@@ -130,7 +130,11 @@ int solve_static(MatDesc &M, const double *d, const double *e, int range, double
     const int max_tries = (opts && opts->max_shift_tries > 0) ? opts->max_shift_tries : 8;
     const unsigned fault_mask = opts ? opts->fault_mask : 0u;
     const int tpe = opts ? opts->tpe : 0;
+    const int bwarps = (opts && opts->bisect_warps > 0 && opts->bisect_warps <= 64) ? opts->bisect_warps : 48;
     const int max_depth = (opts && opts->max_depth > 0) ? opts->max_depth : 64;
+    // the absolute-gap split is not taken here: the array holds the root's clusters on the
+    // assumption that each has two members or more
+    const int erep = (opts && opts->erep) ? 1 : 0;
     const long long n = M.n;
 
     MatDesc *dmats = ar.low<MatDesc>(1);
@@ -187,7 +191,8 @@ int solve_static(MatDesc &M, const double *d, const double *e, int range, double
     LevelCounters *ctr = ar.low<LevelCounters>(1);
     int *work = ar.low<int>(1);
     // RQI scratch: up to a quarter of the array, at most one warp slot per 4 singletons
-    const int team = 8; // lanes per singleton (the latency-bound choice for one matrix)
+    // lanes per singleton: 8 (the latency-bound choice for one matrix) unless forced
+    const int team = (opts && (opts->rqi_team == 2 || opts->rqi_team == 8)) ? opts->rqi_team : 8;
     const size_t slot_bytes = (size_t)rqi_scratch_per_index(team) * n * sizeof(double);
     const long long want_slots = (mtotal + rqi_singles_per_slot(team) - 1) / rqi_singles_per_slot(team);
     const long long cap_slots = std::max<long long>(1, (MR3_STATIC_SCRATCH_BYTES / 4) / slot_bytes);
@@ -202,7 +207,7 @@ int solve_static(MatDesc &M, const double *d, const double *e, int range, double
     if (range != MR3_RANGE_ALL) launch_outer_gaps(nblk, blks, nodes0, pool0, rtol, dinfo, s);
     if (M.nblk > 1) launch_zero_z(1, dmats, Z, s);
     launch_grid(nblk, blks, nodes0, pool0, grid, lo, hi, M.m, dinfo, s);
-    launch_bisect((int)ncols, nullptr, lanes_auto(mtotal, tpe), (int)ncols, cnode, nodes0, blks,
+    launch_bisect((int)ncols, nullptr, lanes_auto(mtotal, tpe, bwarps), (int)ncols, cnode, nodes0, blks,
                   pool0, jloc, lo, hi, rtol, nullptr, dinfo, s);
 
     // ---- level loop, all on stream s: classify; singletons by RQI; clusters shifted and
@@ -213,7 +218,7 @@ int solve_static(MatDesc &M, const double *d, const double *e, int range, double
     int status = 0;
     for (int level = 0;; ++level) {
         SCK(cudaMemsetAsync(ctr, 0, sizeof(LevelCounters), s));
-        launch_classify(ncur, cur_nodes, blks, lo, hi, gaptol, gapl, gapr, singles, clusters,
+        launch_classify(ncur, cur_nodes, blks, lo, hi, gaptol, 0.0, gapl, gapr, singles, clusters,
                         crep, cnode, ctr, dinfo, s);
         LevelCounters hc;
         SCK(cudaMemcpyAsync(&hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, s));
@@ -234,9 +239,9 @@ int solve_static(MatDesc &M, const double *d, const double *e, int range, double
         SFULL(ar);
         launch_refine_ends(hc.ncluster, clusters, cur_nodes, blks, cur_pool, jloc, lo, hi, tri, dinfo, s);
         launch_shift(hc.ncluster, clusters, crep, cur_nodes, blks, cur_pool, next_pool, next_nodes,
-                     tau, cnode, next_active, jloc, lo, hi, max_tries, fault_mask, tri, shift_ws,
-                     dinfo, s);
-        launch_bisect(hc.nactive, next_active, lanes_auto(hc.nactive, tpe), (int)ncols, cnode,
+                     tau, cnode, next_active, jloc, lo, hi, max_tries, fault_mask, erep, tri,
+                     shift_ws, dinfo, s);
+        launch_bisect(hc.nactive, next_active, lanes_auto(hc.nactive, tpe, bwarps), (int)ncols, cnode,
                       next_nodes, blks, next_pool, jloc, lo, hi, rtol, tau, dinfo, s);
         cur_pool = next_pool;
         cur_nodes = next_nodes;
@@ -245,7 +250,7 @@ int solve_static(MatDesc &M, const double *d, const double *e, int range, double
             // depth cap: the remaining members are finished as singletons (flagged)
             status = MR3_SDEPTH;
             SCK(cudaMemsetAsync(ctr, 0, sizeof(LevelCounters), s));
-            launch_classify(ncur, cur_nodes, blks, lo, hi, -1e308, gapl, gapr, singles, clusters,
+            launch_classify(ncur, cur_nodes, blks, lo, hi, -1e308, 0.0, gapl, gapr, singles, clusters,
                             crep, cnode, ctr, dinfo, s);
             SCK(cudaMemcpyAsync(&hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, s));
             SCK(cudaStreamSynchronize(s));

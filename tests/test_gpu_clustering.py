@@ -2,10 +2,12 @@
 (tests/golden/clustering_rho.txt: Ch. 5 Table tab:clustering and Table
 tab:clusteringdouble).  rho = largest cluster / n; rho = 1/n means no cluster at all.
 
-The binary64 rows were measured with LAPACK's DSTEMR; the classification criterion is
+The binary64 rows of criterion I were measured with LAPACK's DSTEMR; the classification criterion is
 the same (reldist >= 1e-3 on classification-accuracy intervals; the automatic gaptol of
 this solver is 1e-3 at these orders), and this solver's rho agrees to half a unit of the
-printed second decimal.  The mixed-precision rows are
+printed second decimal.  The rows of criterion II (tree "fp64abs": gaptol 1e-3 with the
+root's classification amended by absolute gaps, the solver's default) run with
+opts.abs_split on, the others with it off.  The mixed-precision rows are
 structural (no cluster, or only the Wilkinson pairs) and are matched exactly."""
 import os
 
@@ -50,12 +52,14 @@ def test_clustering_matches_thesis(cuda, fam, n, tree, rho):
     import paper_1401_4950_gb300 as mr3
     d, e = _matrix(fam, n)
     dt, et = torch.tensor(d, device="cuda"), torch.tensor(e, device="cuda")
-    prec = mr3.FP64 if tree == "fp64" else mr3.DD
-    _, _, info = mr3.stemr(dt, et, opts=mr3.make_opts(prec=prec))
+    prec = mr3.DD if tree == "mixed" else mr3.FP64
+    # criterion I: relative gaps only; criterion II: the default absolute-gap amendment
+    opts = mr3.make_opts(prec=prec, abs_split=0 if tree == "fp64abs" else -1)
+    _, _, info = mr3.stemr(dt, et, opts=opts)
     torch.cuda.synchronize()
     nn = len(d)
     ours = max(info["largest_cluster"], 1) / nn
-    if tree == "fp64":
+    if tree in ("fp64", "fp64abs"):
         assert abs(ours - rho) <= 0.005, (ours, rho)
     else:
         assert round(ours * n) == round(rho * n), (ours, rho)
