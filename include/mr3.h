@@ -86,8 +86,13 @@ typedef struct {
                                   spdiam / (n_b - 1) (the relative criterion amended by
                                   absolute gaps, Sec. 3.2.3, Sec. 4.2.1); the pieces cut out
                                   of a relative cluster get their own representations.
-                                  0 or positive = on, negative = off (relative gaps only).
-                                  mr3_stemr_static never applies it [0: on]                  */
+                                  Positive = on.  Caution: those representations are shifted
+                                  into the interior of the root's spectrum, where element
+                                  growth can fail the growth test on every candidate (near-
+                                  Toeplitz spectra); they are then accepted by least growth,
+                                  the call returns MR3_SUNTESTED_RRR, and orthogonality is
+                                  no longer guaranteed.  mr3_stemr_static never applies it
+                                  [0: relative gaps only]                                    */
     int erep;                  /* nonzero: binary64 child representations are kept as
                                   e-representations (d, beta): the off-diagonal entries are
                                   shared with the root instead of recomputed as d+ l+ (Ch. 3,

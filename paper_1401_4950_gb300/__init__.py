@@ -120,7 +120,7 @@ def make_opts(prec=FP64, gaptol=0.0, seed=0, max_rqi=0, max_shift_tries=0, fault
     o.prec, o.gaptol, o.seed, o.max_rqi = prec, gaptol, seed, max_rqi
     o.max_shift_tries, o.fault_mask, o.tpe, o.max_depth = max_shift_tries, fault_mask, tpe, max_depth
     o.profile, o.rqi_team, o.bisect_warps = profile, rqi_team, bisect_warps
-    # abs_split: 0 (default) or positive = absolute-gap amendment on, negative = off
+    # abs_split: positive = absolute-gap amendment at the root on (default off)
     o.abs_split, o.erep = int(abs_split), int(bool(erep))
     return o
 

@@ -49,7 +49,7 @@ Opts resolve(const mr3_opts *o) {
     r.rqi_team = (o && (o->rqi_team == 2 || o->rqi_team == 8)) ? o->rqi_team : 0;
     r.bisect_warps = (o && o->bisect_warps > 0 && o->bisect_warps <= 64) ? o->bisect_warps
                                                                          : MR3_BISECT_WARPS_PER_SM;
-    r.abs_split = (o && o->abs_split < 0) ? 0 : 1;
+    r.abs_split = (o && o->abs_split > 0) ? 1 : 0;
     r.erep = (o && o->erep) ? 1 : 0;
     return r;
 }

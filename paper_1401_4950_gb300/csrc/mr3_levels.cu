@@ -444,8 +444,9 @@ void launch_classify(int nnode, const Node *nodes, const BlkDesc *blks, const do
 // copy), phase 1 checks those bounds with binary64 counts, widens where they fail, and
 // continues in binary64 with fewer lanes per end (the binary64 pipe, not latency, bounds
 // it when ends are many).  A cluster of one member (cut out by the absolute-gap split) has
-// no inner neighbour: its one eigenvalue is refined to full accuracy by the group of its
-// left end, and the group of its right end stays idle.
+// no inner neighbour: the group of its left end refines its one eigenvalue below 1e-3 of
+// the smaller gap to its outer neighbours (so that the shift next to it leaves it with a
+// relative gap of about 1e3 in the child), and the group of its right end stays idle.
 __global__ void k_refine_ends(int ncluster, const ClusterItem *__restrict__ clusters,
                               const Node *__restrict__ nodes, const BlkDesc *__restrict__ blks,
                               const double *__restrict__ pool, const int *__restrict__ jloc,
@@ -472,7 +473,14 @@ __global__ void k_refine_ends(int ncluster, const ClusterItem *__restrict__ clus
         tgt = jloc[col];
         L = lo[col];
         H = hi[col];
-        nb = (C.c0 == C.c1) ? -INFINITY : (side ? hi[col - 1] : lo[col + 1]);
+        if (C.c0 == C.c1) {
+            // a lower bound on the right neighbour that also bounds the gap to the left one:
+            // the bisection tolerance then follows min(left gap, right gap)
+            const double gmin = fmin(L - C.lnb, C.rnb - H);
+            nb = (gmin > 0.0 && gmin < INFINITY) ? H + gmin : -INFINITY;
+        } else {
+            nb = side ? hi[col - 1] : lo[col + 1];
+        }
         // phase 1 resumes with the neighbour bound phase 0 tightened
         if (phase == 1) nb = carry[g].x;
     }

@@ -1,10 +1,9 @@
 """The classification and representation options of the tree, against the CPU oracle at
 the same 10 n eps gates:
 
-* abs_split (on by default; negative turns it off): the root classification amended by
-  absolute gaps (Sec. 3.2.3, Sec. 4.2.1); pieces of a relative cluster separated by at
-  least the block's average gap get their own child representations, one-member pieces
-  included;
+* abs_split (opt-in): the root classification amended by absolute gaps (Sec. 3.2.3,
+  Sec. 4.2.1); pieces of a relative cluster separated by at least the block's average gap
+  get their own child representations, one-member pieces included;
 * erep: binary64 child representations kept as e-representations (d, beta), the
   off-diagonal entries shared with the root (Ch. 3, representation forms).
 """
@@ -22,8 +21,8 @@ CASES = [("random", 2), ("random", 37), ("random", 1000), ("one_two_one", 100),
          ("legendre", 300), ("laguerre", 300), ("hermite", 400), ("hermite", 2000),
          ("uniform_eigs", 1000), ("geometric_eigs", 1000)]
 
-FLAGS = [{"abs_split": -1}, {"erep": 1}, {"abs_split": -1, "erep": 1}]
-IDS = ["relative-only", "erep", "relative-only+erep"]
+FLAGS = [{"abs_split": 1}, {"erep": 1}, {"abs_split": 1, "erep": 1}]
+IDS = ["abs", "erep", "abs+erep"]
 
 
 def _solve(d, e, prec=0, rng="A", il=1, iu=None, **flags):
@@ -59,10 +58,10 @@ def test_index_range(cuda, kind, n, il, iu, flags):
 
 @pytest.mark.parametrize("kind,n", [("one_two_one", 1000), ("hermite", 1500), ("random", 800),
                                     ("wilkinson", 201)])
-def test_double_double_tree_relative_only(cuda, kind, n):
+def test_double_double_tree_with_abs_split(cuda, kind, n):
     import paper_1401_4950_gb300 as mr3
     d, e = tm.make(kind, n, seed=103)
-    w, Z, info = _solve(d, e, prec=mr3.DD, abs_split=-1)
+    w, Z, info = _solve(d, e, prec=mr3.DD, abs_split=1)
     check_eigenpairs(d, e, w, Z)
 
 
@@ -73,8 +72,8 @@ def test_abs_split_shrinks_the_largest_cluster(cuda, kind, n, shrinks):
     # It shrinks where the spacing varies (1-2-1, Hermite); on an equispaced spectrum every
     # gap is the average gap and nothing splits.
     d, e = tm.FAMILIES[kind](n, device="cuda") if kind == "uniform_eigs" else tm.make(kind, n, seed=104)
-    _, _, i0 = _solve(d, e, abs_split=-1)
-    _, _, i1 = _solve(d, e)
+    _, _, i0 = _solve(d, e)
+    _, _, i1 = _solve(d, e, abs_split=1)
     assert i1["largest_cluster"] <= i0["largest_cluster"], (i0, i1)
     if shrinks:
         assert i1["largest_cluster"] < i0["largest_cluster"], (i0, i1)
@@ -93,13 +92,30 @@ def test_batched_matches_per_matrix_with_flags(cuda):
     n_off[1:] = np.cumsum(sizes)
     d = np.concatenate([m[0] for m in mats])
     e = np.concatenate([np.r_[m[1], 0.0] for m in mats])
-    o = mr3.make_opts(erep=1)
+    o = mr3.make_opts(abs_split=1, erep=1)
     _, w, Z, z_off, _ = mr3.stemr_batched(n_off, torch.tensor(d, device="cuda"),
                                           torch.tensor(e, device="cuda"), opts=o)
     for b, n in enumerate(sizes):
-        ws, _, _ = _solve(*mats[b], erep=1)
+        ws, _, _ = _solve(*mats[b], abs_split=1, erep=1)
         wb = w[n_off[b]:n_off[b] + n].cpu().numpy()
         Zb = Z[z_off[b]:z_off[b] + n * n].view(n, n).t().cpu().numpy()
         tn = max(abs(ws[0]), abs(ws[-1]))
         assert np.max(np.abs(wb - ws)) <= 4 * n * 2.0 ** -53 * tn
         check_eigenpairs(*mats[b], wb, Zb)
+
+
+def test_abs_split_warns_when_interior_shifts_fail(cuda):
+    # T = I + 1e-12 J (near-Toeplitz): every piece the absolute-gap split cuts out needs a
+    # shift inside the root's spectrum, where the element growth of L D L^T - tau I exceeds
+    # the growth test for every candidate.  The representations are then accepted by least
+    # growth (Alg. "Shifting the spectrum": accuracy no longer guaranteed), which the call
+    # reports as status 1; the default classification (relative gaps only) shifts the one
+    # big cluster outside the spectrum and stays at the gates.
+    n = 500
+    d, e = np.ones(n), np.full(n - 1, 1e-12)
+    w, Z, info = _solve(d, e, abs_split=1)
+    assert info["status"] == 1 and info["untested_rrr"] > 0, info
+    w, Z, info = _solve(d, e)
+    assert info["status"] == 0 and info["untested_rrr"] == 0
+    check_eigenpairs(d, e, w, Z, w_ref=np.sort(1.0 + 2e-12 * np.cos(np.pi * np.arange(1, n + 1) / (n + 1))),
+                     tn=1.0, vec_compare=False)

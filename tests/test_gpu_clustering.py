@@ -6,8 +6,7 @@ The binary64 rows of criterion I were measured with LAPACK's DSTEMR; the classif
 the same (reldist >= 1e-3 on classification-accuracy intervals; the automatic gaptol of
 this solver is 1e-3 at these orders), and this solver's rho agrees to half a unit of the
 printed second decimal.  The rows of criterion II (tree "fp64abs": gaptol 1e-3 with the
-root's classification amended by absolute gaps, the solver's default) run with
-opts.abs_split on, the others with it off.  The mixed-precision rows are
+root's classification amended by absolute gaps) run with opts.abs_split on.  The mixed-precision rows are
 structural (no cluster, or only the Wilkinson pairs) and are matched exactly."""
 import os
 
@@ -53,8 +52,8 @@ def test_clustering_matches_thesis(cuda, fam, n, tree, rho):
     d, e = _matrix(fam, n)
     dt, et = torch.tensor(d, device="cuda"), torch.tensor(e, device="cuda")
     prec = mr3.DD if tree == "mixed" else mr3.FP64
-    # criterion I: relative gaps only; criterion II: the default absolute-gap amendment
-    opts = mr3.make_opts(prec=prec, abs_split=0 if tree == "fp64abs" else -1)
+    # criterion I: relative gaps only (the default); criterion II: the absolute-gap amendment
+    opts = mr3.make_opts(prec=prec, abs_split=1 if tree == "fp64abs" else 0)
     _, _, info = mr3.stemr(dt, et, opts=opts)
     torch.cuda.synchronize()
     nn = len(d)

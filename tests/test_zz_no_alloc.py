@@ -25,9 +25,7 @@ def _both(d, e, **kw):
     import torch
     import paper_1401_4950_gb300 as mr3
     dt, et = _dev(d), _dev(e)
-    # the static entry point classifies by relative gaps only (its array holds clusters of
-    # two members or more): the reference solve does the same
-    w0, Z0, i0 = mr3.stemr(dt, et, opts=mr3.make_opts(abs_split=-1), **kw)
+    w0, Z0, i0 = mr3.stemr(dt, et, **kw)
     runs = []
     for _ in range(2):  # two calls in a row on the same array
         w1, Z1, i1 = mr3.stemr_static(dt, et, **kw)
