@@ -138,6 +138,12 @@ typedef struct {
        5 cluster shifts, 6 refinement on child representations, 7 output ordering. */
     double kernel_ms[8];
     int kernel_launches[8];
+    int ladder_clusters;       /* clusters whose first two shift candidates (tau_l, tau_r at
+                                  the refined ends) both failed the plain growth test       */
+    int recomputed_rrr;        /* ... of those, clusters a back-off candidate then passed  */
+    int envelope_rrr;          /* ... of those, clusters a first candidate of which passed
+                                  the envelope-weighted growth test (Alg. "Shifting the
+                                  spectrum", remark 3)                                      */
 } mr3_info;
 
 /*

@@ -48,7 +48,8 @@ class Info(ctypes.Structure):
                 ("bisect_fallbacks", ctypes.c_int), ("sturm_steps", ctypes.c_longlong),
                 ("shift_steps", ctypes.c_longlong), ("twisted_steps", ctypes.c_longlong),
                 ("status_counts", ctypes.c_int * 8), ("kernel_ms", ctypes.c_double * 8),
-                ("kernel_launches", ctypes.c_int * 8)]
+                ("kernel_launches", ctypes.c_int * 8), ("ladder_clusters", ctypes.c_int),
+                ("recomputed_rrr", ctypes.c_int), ("envelope_rrr", ctypes.c_int)]
 
     _ARRAYS = ("status_counts", "kernel_ms", "kernel_launches")
 

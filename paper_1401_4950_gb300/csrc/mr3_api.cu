@@ -557,6 +557,9 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
     out.shift_steps = (long long)hi_info.shift_steps;
     prof.collect(out);
     out.twisted_steps = (long long)hi_info.twisted_steps;
+    out.ladder_clusters = hi_info.ladder;
+    out.recomputed_rrr = hi_info.recomputed;
+    out.envelope_rrr = hi_info.env_accepted;
     for (int k = 0; k < 8; ++k) out.status_counts[k] = hi_info.status[k];
     if (status) out.status_counts[status] += 1;
     if (info) *info = out;

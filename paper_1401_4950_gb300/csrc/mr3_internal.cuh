@@ -119,6 +119,9 @@ struct DevInfo {
     int largest;
     int dmax;
     int status[8];
+    int ladder;       // clusters whose first two shift candidates failed the plain test
+    int recomputed;   // ... of which a back-off candidate passed the growth test
+    int env_accepted; // ... of which a first candidate passed the envelope test
 };
 
 // ------------------------------------------------------------------ bit helpers
@@ -130,6 +133,14 @@ __device__ __forceinline__ int biased_exp(double x) {
     return (int)((__double_as_longlong(x) >> 52) & 0x7ff);
 }
 // 2^k for -1022 <= k <= 1023 (exact power of two built from the exponent field).
+// Approximate reciprocal of the hardware (rcp.approx.ftz.f64): for magnitudes in tests
+// that need no correct rounding.
+__device__ __forceinline__ double rcp_approx(double x) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    return r;
+}
+
 __device__ __forceinline__ double pow2i(int k) {
     return __longlong_as_double((long long)(k + 1023) << 52);
 }

@@ -682,6 +682,43 @@ __device__ void trial_shift(int n, const double *__restrict__ d, const double *_
     growth = exists ? g : INFINITY;
 }
 
+// Backward progressive recurrence of L D L^T - tau I (Alg. dqds): p_{n-1} = d_{n-1} - tau,
+// p_k = d_k p_{k+1} / (p_{k+1} + dll_k) - tau, in homogeneous form p = N / M with no
+// division on the chain:  M_k = N + dll_k M,  N_k = (d_k - tau) N - (tau dll_k) M,
+// rescaled by a power of two every eight steps (an overflow inside a block gives a
+// non-finite value, which the envelope test treats as a failure).  Stores N_k, M_k.
+__device__ void dqds_backward_store(int n, const double *__restrict__ d,
+                                    const double *__restrict__ dll, double tau, double *Ns,
+                                    double *Ms) {
+    double N = __ldg(d + n - 1) - tau, M = 1.0;
+    Ns[n - 1] = N;
+    Ms[n - 1] = M;
+    int k = n - 2;
+    for (; k >= 7; k -= 8) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const double dk = __ldg(d + k - u), lk = __ldg(dll + k - u);
+            const double Mk = fma(lk, M, N);
+            N = fma(dk - tau, N, -(tau * lk) * M);
+            M = Mk;
+            Ns[k - u] = N;
+            Ms[k - u] = M;
+        }
+        const int ex = biased_exp(M);
+        const double sc = (ex > 0 && ex < 0x7ff) ? pow2i(1023 - ex) : 1.0;
+        N *= sc;
+        M *= sc;
+    }
+    for (; k >= 0; --k) {
+        const double dk = __ldg(d + k), lk = __ldg(dll + k);
+        const double Mk = fma(lk, M, N);
+        N = fma(dk - tau, N, -(tau * lk) * M);
+        M = Mk;
+        Ns[k] = N;
+        Ms[k] = M;
+    }
+}
+
 // The first two candidates of every cluster, one lane each (16 clusters per warp):
 // tau_l = lo_p - 100 eps |lo_p| on even lanes, tau_r = hi_q + 100 eps |hi_q| on odd lanes.
 // Each stores its c_i and rescale exponents in the child's slots (tau_l: d, tau_r: dl;
@@ -741,17 +778,165 @@ __device__ __forceinline__ ShiftSetup shift_setup(const ClusterItem &C, const Bl
     return S;
 }
 
+// Clusters per launch from which the envelope test runs before the back-off ladder
+// (throughput regime) instead of beside it (latency regime): four warps per SM.
+constexpr int kEnvSequentialClusters = 152 * 32 * 4;
+
 __host__ __device__ __forceinline__ int ladder_width(int max_tries) {
     return 2 * (max(2, min(max_tries, 16)) - 1);
 }
 
+// The "more sophisticated test" of Alg. "Shifting the spectrum" (remark 3), for the
+// clusters whose first candidates failed the plain growth test: element growth is
+// harmless where every eigenvector of the cluster is small, so the growth of a first
+// candidate is weighed by a bound on the envelope of the cluster's invariant subspace,
+// env2(k) = sum_{j in cluster} z_j(k)^2.  With mu_j = lambda_j - tau the child's
+// eigenvalues and gamma_k the twist element of L D L^T - tau I at k (Alg. Getvec:
+// gamma_k = s_k + p_k + tau from the forward and backward recurrences),
+//   1 / gamma_k = [(L D L^T - tau I)^{-1}]_kk = sum_j z_j(k)^2 / mu_j;
+// the cluster's mu_j share one sign (tau lies outside the cluster) and are at most Lambda
+// in magnitude (the cluster's far end seen from tau), every other |mu_j| is at least g
+// (the distance from tau to the nearest eigenvalue outside the cluster), so
+//   env2(k) <= Lambda (1 / |gamma_k| + 1 / g)   (capped at 1).
+// The candidate passes when
+//   max_k ( |d+_k| env2(k) + |dll+_k| env2(k+1) ) <= 8 spdiam(M_root),
+// the plain test's threshold applied to the z-weighted pivots of z^T L+ |D+| L+^T z.
+// Over the clusters queued by k_shift_select (threads past the queue's length return):
+// shift_envback, one lane per first candidate in warps of their own inside the back-off
+// ladder's launch (the two chains of n steps run side by side), runs the backward
+// recurrence (N, M of tau_l at [3n, 5n) of the child's slot, of tau_r at [5n, 7n));
+// k_shift_envtest, one warp per cluster with the indices split over the lanes, forms
+// s_k = d+_k - d_k from the trial's stored c_k and p_k = N_k / M_k, reduces the weighted
+// growth, and takes the better passing candidate, which k_shift_pick then keeps over the
+// ladder.  The test needs magnitudes only: its divisions use the hardware's approximate
+// reciprocal (rcp.approx.ftz.f64); and since env2 <= 1, an index whose |d+_k| + |dll+_k|
+// is below the threshold cannot fail it, so the envelope is formed only around the others.
+__device__ unsigned long long shift_envback(long long t, int nslots,
+                                            const ClusterItem *__restrict__ clusters,
+                                            const long long *__restrict__ cluster_rep,
+                                            const Node *__restrict__ nodes,
+                                            const BlkDesc *__restrict__ blks,
+                                            const double *__restrict__ pool, double *childpool,
+                                            const double *__restrict__ lo,
+                                            const double *__restrict__ hi,
+                                            const double2 *__restrict__ tri, unsigned fault_mask,
+                                            const int *__restrict__ ladder,
+                                            const int *__restrict__ counts) {
+    const int li = (int)(t >> 1), side = (int)(t & 1);
+    unsigned long long steps = 0;
+    if (li < nslots && li < counts[0]) {
+        const int ci = ladder[li];
+        if (tri[2 * ci + side].x != 0.0) {
+            const ClusterItem C = clusters[ci];
+            const Node P = nodes[C.node];
+            const int n = blks[P.blk].n;
+            const double *pd = pool + P.rep;
+            double *Ns = childpool + cluster_rep[ci] + 3ll * n + 2ll * n * side;
+            const double Lp = lo[C.c0], Hq = hi[C.c1];
+            double tau = side ? Hq + MR3_TAU_OFFSET * kEps * fabs(Hq)
+                              : Lp - MR3_TAU_OFFSET * kEps * fabs(Lp);
+            if (side == 0 && (fault_mask & MR3_FAULT_NAN_SHIFT)) tau = NAN;
+            dqds_backward_store(n, pd, pd + 2 * n, tau, Ns, Ns + n);
+            steps = n;
+        }
+    }
+    return steps;
+}
+
+__global__ void k_shift_envtest(int nslots, const ClusterItem *__restrict__ clusters,
+                                const long long *__restrict__ cluster_rep,
+                                const Node *__restrict__ nodes, const BlkDesc *__restrict__ blks,
+                                const double *__restrict__ pool,
+                                const double *__restrict__ childpool,
+                                const double *__restrict__ lo, const double *__restrict__ hi,
+                                const double2 *__restrict__ tri, unsigned fault_mask,
+                                const int *__restrict__ ladder, const int *__restrict__ counts,
+                                ShiftDecision *dec, DevInfo *info) {
+    const int li = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (li >= nslots || li >= counts[0]) return; // whole warps
+    if (fault_mask & MR3_FAULT_SHIFT_REJECT) return;
+    const int ci = ladder[li];
+    const ClusterItem C = clusters[ci];
+    const Node P = nodes[C.node];
+    const int n = blks[P.blk].n;
+    const double *pd = pool + P.rep, *pdl = pd + n;
+    const double *cd = childpool + cluster_rep[ci];
+    const double Lp = lo[C.c0], Hq = hi[C.c1];
+    double wside[2] = {INFINITY, INFINITY};
+    for (int side = 0; side < 2; ++side) {
+        double tau = side ? Hq + MR3_TAU_OFFSET * kEps * fabs(Hq) : Lp - MR3_TAU_OFFSET * kEps * fabs(Lp);
+        if (side == 0 && (fault_mask & MR3_FAULT_NAN_SHIFT)) tau = NAN;
+        const double Lam = side ? tau - Lp : Hq - tau;
+        const double g = fmin(tau - C.lnb, C.rnb - tau);
+        if (tri[2 * ci + side].x == 0.0 || !(g > 0.0) || !(Lam > 0.0)) continue;
+        const double ig = 1.0 / g;
+        const double *U = side ? cd + n : cd;
+        const int *K = (const int *)(cd + 2 * n) + side;
+        const double *Ns = cd + 3ll * n + 2ll * n * side, *Ms = Ns + n;
+        // d+_k = U[k] / U[k-1] 2^-K[k-1] (U[-1] = 1, K[-1] = 0); env2 bound at k
+        auto dplus = [&](int k) {
+            const double um = (k > 0) ? U[k - 1] : 1.0;
+            const int km = (k > 0) ? K[2 * (k - 1)] : 0;
+            return U[k] * rcp_approx(um) * pow2i(-km);
+        };
+        auto env_at = [&](int k, double dk) {
+            const double gam = (dk - pd[k]) + Ns[k] * rcp_approx(Ms[k]) + tau;
+            return fmin(1.0, Lam * (fabs(rcp_approx(gam)) + ig));
+        };
+        // term_k <= |d+_k| + |dll+_k| (env2 <= 1): only the indices where that sum exceeds
+        // the threshold need the envelope (theirs and the next one's)
+        const double thr = 8.0 * blks[P.blk].spdiam;
+        double wg = 0.0;
+        bool carry_need = false; // the previous chunk's last index needs env2 of this chunk's first
+        for (int base = 0; base < n; base += 32) {
+            const int k = base + lane;
+            double dk = 0.0, dllk = 0.0;
+            if (k < n) {
+                dk = dplus(k);
+                if (k < n - 1) {
+                    const double dl = pdl[k];
+                    dllk = fabs(dl * dl * rcp_approx(dk));
+                }
+            }
+            const double mag = fabs(dk) + dllk;
+            const bool need = (k < n) && !(mag <= thr);
+            const bool need_prev_raw = __shfl_up_sync(FULL_MASK, need && dllk != 0.0, 1);
+            const bool need_prev = (lane == 0) ? carry_need : need_prev_raw;
+            carry_need = __shfl_sync(FULL_MASK, need && dllk != 0.0, 31);
+            double env = 0.0;
+            if (k < n && (need || need_prev)) env = env_at(k, dk);
+            double env_next = __shfl_down_sync(FULL_MASK, env, 1);
+            if (lane == 31 && need && dllk != 0.0 && k + 1 < n) env_next = env_at(k + 1, dplus(k + 1));
+            if (need) {
+                const double term = fabs(dk) * env + dllk * env_next;
+                wg = (term > wg || term != term) ? term : wg;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double v = __shfl_xor_sync(FULL_MASK, wg, o);
+            wg = (v > wg || v != v) ? v : wg;
+        }
+        wside[side] = (wg == wg) ? wg : INFINITY;
+    }
+    if (lane == 0) {
+        const ShiftSetup S = shift_setup(C, blks[P.blk], lo, hi);
+        const bool v0 = wside[0] <= S.thresh, v1 = wside[1] <= S.thresh;
+        if (v0 || v1) {
+            const int se = (v0 && (!v1 || wside[0] <= wside[1])) ? 0 : 1;
+            dec[ci] = {se ? S.tau_r0 : S.tau_l0, se, 0};
+            atomicAdd(&info->env_accepted, 1);
+        }
+    }
+}
+
 // One thread per cluster: take the better existing first candidate if its growth passes,
-// else queue the cluster for the back-off ladder.
+// else queue the cluster for the envelope test and the back-off ladder.
 __global__ void k_shift_select(int ncluster, const ClusterItem *__restrict__ clusters,
                                const Node *__restrict__ nodes, const BlkDesc *__restrict__ blks,
                                const double *__restrict__ lo, const double *__restrict__ hi,
                                unsigned fault_mask, const double2 *__restrict__ tri,
-                               ShiftDecision *dec, int *ladder, int *counts) {
+                               ShiftDecision *dec, int *ladder, int *counts, DevInfo *info) {
     const int ci = blockIdx.x * blockDim.x + threadIdx.x;
     if (ci >= ncluster) return;
     const ClusterItem C = clusters[ci];
@@ -769,21 +954,36 @@ __global__ void k_shift_select(int ncluster, const ClusterItem *__restrict__ clu
     } else {
         dec[ci] = {0.0, -1, 0};
         ladder[atomicAdd(counts, 1)] = ci;
+        atomicAdd(&info->ladder, 1);
     }
 }
 
 // One lane per back-off candidate: tau_l0 - 2^(t-1) delta (even j) and
-// tau_r0 + 2^(t-1) delta (odd j), t = j / 2 + 1, for every queued cluster.
+// tau_r0 + 2^(t-1) delta (odd j), t = j / 2 + 1, for every queued cluster that the
+// envelope test did not settle.
+// Blocks from ladder_blocks on run shift_envback instead.
 __global__ void k_shift_ladder(int nslots, int max_tries, const ClusterItem *__restrict__ clusters,
+                               const long long *__restrict__ cluster_rep,
                                const Node *__restrict__ nodes, const BlkDesc *__restrict__ blks,
-                               const double *__restrict__ pool, const double *__restrict__ lo,
-                               const double *__restrict__ hi, const int *__restrict__ ladder,
-                               const int *__restrict__ counts, double2 *lad, DevInfo *info) {
+                               const double *__restrict__ pool, double *childpool,
+                               const double *__restrict__ lo, const double *__restrict__ hi,
+                               const double2 *__restrict__ tri, unsigned fault_mask,
+                               const int *__restrict__ ladder, const int *__restrict__ counts,
+                               const ShiftDecision *__restrict__ dec, double2 *lad,
+                               unsigned ladder_blocks, DevInfo *info) {
+    unsigned long long steps = 0;
+    if (blockIdx.x >= ladder_blocks) {
+        const long long t = (long long)(blockIdx.x - ladder_blocks) * blockDim.x + threadIdx.x;
+        steps = shift_envback(t, nslots, clusters, cluster_rep, nodes, blks, pool, childpool, lo,
+                              hi, tri, fault_mask, ladder, counts);
+        for (int o = 16; o > 0; o >>= 1) steps += __shfl_xor_sync(FULL_MASK, steps, o);
+        if ((threadIdx.x & 31) == 0 && steps) atomicAdd(&info->shift_steps, steps);
+        return;
+    }
     const int NL = ladder_width(max_tries);
     const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int li = (int)(gid / NL), j = (int)(gid % NL);
-    unsigned long long steps = 0;
-    if (li < nslots && li < counts[0]) {
+    if (li < nslots && li < counts[0] && dec[ladder[li]].win < 0) {
         const int ci = ladder[li];
         const ClusterItem C = clusters[ci];
         const Node P = nodes[C.node];
@@ -812,11 +1012,12 @@ __global__ void k_shift_pick(int nslots, int max_tries, unsigned fault_mask,
                              const double *__restrict__ lo, const double *__restrict__ hi,
                              const double2 *__restrict__ tri, const int *__restrict__ ladder,
                              int *counts, const double2 *__restrict__ lad, ShiftDecision *dec,
-                             int *recomp) {
+                             int *recomp, DevInfo *info) {
     const int li = blockIdx.x * blockDim.x + threadIdx.x;
     if (li >= nslots || li >= counts[0]) return;
     const int NL = ladder_width(max_tries);
     const int ci = ladder[li];
+    if (dec[ci].win >= 0) return; // settled by the envelope test
     const ClusterItem C = clusters[ci];
     const ShiftSetup S = shift_setup(C, blks[nodes[C.node].blk], lo, hi);
     const bool reject_all = (fault_mask & MR3_FAULT_SHIFT_REJECT) != 0;
@@ -847,7 +1048,10 @@ __global__ void k_shift_pick(int nslots, int max_tries, unsigned fault_mask,
         else D = {S.tau_l0, 0, 1}; // nothing exists: keep the first candidate (flagged)
     }
     dec[ci] = D;
-    if (D.win == 2) recomp[atomicAdd(counts + 1, 1)] = ci;
+    if (D.win == 2) {
+        recomp[atomicAdd(counts + 1, 1)] = ci;
+        if (!D.untested) atomicAdd(&info->recomputed, 1);
+    }
 }
 
 // One lane per cluster whose winner is a back-off candidate: its factorization again,
@@ -1004,12 +1208,36 @@ void launch_shift(int ncluster, const ClusterItem *clusters, const long long *cl
         info);
     const unsigned cb = (unsigned)((ncluster + 127) / 128);
     k_shift_select<<<cb, 128, 0, s>>>(ncluster, clusters, nodes, blks, lo, hi, fault_mask, tri,
-                                      dec, ladder, counts);
-    // back-off ladder for the queued clusters (threads past the queue's length return)
-    k_shift_ladder<<<(unsigned)(((long long)ncluster * NL + 31) / 32), 32, 0, s>>>(
-        ncluster, max_tries, clusters, nodes, blks, pool, lo, hi, ladder, counts, lad, info);
+                                      dec, ladder, counts, info);
+    // back-off ladder and the envelope test's backward recurrences of the queued clusters
+    // (threads past the queue's length return), and the envelope test itself.  Few
+    // clusters (latency bound): the ladder and the recurrences share one launch, and the
+    // ladder's results for clusters the envelope test settles go unused.  Many clusters
+    // (throughput bound): the envelope test first, and the ladder only for the rest.  The
+    // decisions are the same either way.
+    const unsigned lblocks = (unsigned)(((long long)ncluster * NL + 31) / 32);
+    const unsigned eblocks = (unsigned)((2ll * ncluster + 31) / 32);
+    const unsigned tblocks = (unsigned)((ncluster + 3) / 4);
+    if (ncluster < kEnvSequentialClusters) {
+        k_shift_ladder<<<lblocks + eblocks, 32, 0, s>>>(
+            ncluster, max_tries, clusters, cluster_rep, nodes, blks, pool, childpool, lo, hi, tri,
+            fault_mask, ladder, counts, dec, lad, lblocks, info);
+        k_shift_envtest<<<tblocks, 128, 0, s>>>(ncluster, clusters, cluster_rep, nodes, blks, pool,
+                                                childpool, lo, hi, tri, fault_mask, ladder,
+                                                counts, dec, info);
+    } else {
+        k_shift_ladder<<<eblocks, 32, 0, s>>>(
+            ncluster, max_tries, clusters, cluster_rep, nodes, blks, pool, childpool, lo, hi, tri,
+            fault_mask, ladder, counts, dec, lad, 0u, info);
+        k_shift_envtest<<<tblocks, 128, 0, s>>>(ncluster, clusters, cluster_rep, nodes, blks, pool,
+                                                childpool, lo, hi, tri, fault_mask, ladder,
+                                                counts, dec, info);
+        k_shift_ladder<<<lblocks, 32, 0, s>>>(
+            ncluster, max_tries, clusters, cluster_rep, nodes, blks, pool, childpool, lo, hi, tri,
+            fault_mask, ladder, counts, dec, lad, lblocks, info);
+    }
     k_shift_pick<<<cb, 128, 0, s>>>(ncluster, max_tries, fault_mask, clusters, nodes, blks, lo, hi,
-                                    tri, ladder, counts, lad, dec, recomp);
+                                    tri, ladder, counts, lad, dec, recomp, info);
     k_shift_recompute<<<(unsigned)((ncluster + 31) / 32), 32, 0, s>>>(
         ncluster, clusters, cluster_rep, nodes, blks, pool, childpool, recomp, counts, dec, info);
     // conversion to the child representations, one warp per cluster
@@ -1115,7 +1343,8 @@ void launch_sort_outputs(int mi, int m, const MatDesc *mats, double *w, double *
 
 cudaError_t preload_levels() {
     return load_kernels(k_bisect2, k_grid_counts, k_grid_bracket, k_classify, k_refine_ends,
-                        k_shift_trials, k_shift_select, k_shift_ladder, k_shift_pick,
+                        k_shift_trials, k_shift_select, k_shift_envtest,
+                        k_shift_ladder, k_shift_pick,
                         k_shift_recompute, k_shift, k_order_fix, k_rank, k_gather_cols,
                         k_copy_back);
 }

@@ -293,6 +293,9 @@ int solve_static(MatDesc &M, const double *d, const double *e, int range, double
     out.sturm_steps = (long long)h.sturm_steps;
     out.shift_steps = (long long)h.shift_steps;
     out.twisted_steps = (long long)h.twisted_steps;
+    out.ladder_clusters = h.ladder;
+    out.recomputed_rrr = h.recomputed;
+    out.envelope_rrr = h.env_accepted;
     for (int k = 0; k < 8; ++k) out.status_counts[k] = h.status[k];
     if (status) {
         out.status_counts[status] += 1;
