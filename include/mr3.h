@@ -77,7 +77,8 @@ typedef struct {
     int profile;               /* nonzero: time each kernel group with CUDA events on the
                                   call's stream and report it in mr3_info.kernel_ms [0]        */
     int rqi_team;              /* lanes per singleton in the RQI: 0 = auto (2 for many
-                                  singletons, else 8), 2 or 8 to force one [0]               */
+                                  singletons, else 8), 2 or 8 to force one; mr3_stemr_static
+                                  always uses 8 [0]                                          */
     int bisect_warps;          /* bisection lanes per eigenvalue are chosen to keep about this
                                   many warps per SM in flight: 0 = 48, else 1..64 (tpe > 0
                                   overrides) [0]                                              */

@@ -28,6 +28,9 @@ namespace mr3 {
 // normalise the output are exact).  The exponents are kept as integers because they reach
 // tens of thousands (the prefix products Q_i of a glued matrix shrink by the glue at every
 // block): a binary32 logarithm of that size resolves only ~0.4% and drops smaller terms.
+#ifndef MR3_RQI2_MIN_BLOCKS
+#define MR3_RQI2_MIN_BLOCKS 16
+#endif
 constexpr int kRecordDoubles = 4;                    // (X, Y, {S, frac}, {E, int})
 constexpr int kScratchPerSingleton = 2 * kRecordDoubles; // forward and backward record
 
@@ -227,8 +230,16 @@ __device__ __forceinline__ void cand_eval(Cand &c, int i, double xf, double yf, 
 // 1/||z|| and the sign that makes an entry of largest magnitude positive, and forms the
 // Rayleigh quotient of the unit vector with respect to the input T (accuracy remark 5,
 // Sec. 3.1.2), which removes the bias of the root's random perturbation.
+// Resident warps per SM the launch bounds ask for: teams of 2 run where singletons far
+// outnumber the resident warps, so their register budget (128) admits 16 warps per SM, at
+// the price of a few spilled values (measured on the 4096-matrix batch: 12 warps per SM
+// 468 ms, 14: 455, 16: 456, against 557 at the 8 that 213 registers allowed); teams of 8
+// keep the full budget and no stack frame.
+template <int TEAM> struct RqiOccupancy { static constexpr int kMinBlocks = 1; };
+template <> struct RqiOccupancy<2> { static constexpr int kMinBlocks = MR3_RQI2_MIN_BLOCKS; };
+
 template <int TEAM>
-__global__ void __launch_bounds__(32, 1) k_rqi(int nsingle, const SingleItem *__restrict__ singles,
+__global__ void __launch_bounds__(32, RqiOccupancy<TEAM>::kMinBlocks) k_rqi(int nsingle, const SingleItem *__restrict__ singles,
                                             const Node *__restrict__ nodes,
                                             const BlkDesc *__restrict__ blks,
                                             const MatDesc *__restrict__ mats,
@@ -356,8 +367,13 @@ __global__ void __launch_bounds__(32, 1) k_rqi(int nsingle, const SingleItem *__
                             LSum pq;
                             LogG pg;
                             R.get(i, !bw, px, py, pq, pg);
-                            if (bw) cand_eval(cd, i, px, py, pq, pg, xv, yv, lp, lg);
-                            else cand_eval(cd, i, xv, yv, lp, lg, px, py, pq, pg);
+                            // forward pair first: the backward lane passes the record's pair
+                            // as the forward one (selects, so the two lanes stay converged)
+                            const double fx = bw ? px : xv, fy = bw ? py : yv;
+                            const double bx = bw ? xv : px, by = bw ? yv : py;
+                            const LSum fq = bw ? pq : lp, bq = bw ? lp : pq;
+                            const LogG fg = bw ? pg : lg, bg = bw ? lg : pg;
+                            cand_eval(cd, i, fx, fy, fq, fg, bx, by, bq, bg);
                         } else {
                             R.put(i, bw, xv, yv, lp, lg);
                         }

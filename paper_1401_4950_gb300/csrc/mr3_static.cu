@@ -191,8 +191,9 @@ int solve_static(MatDesc &M, const double *d, const double *e, int range, double
     LevelCounters *ctr = ar.low<LevelCounters>(1);
     int *work = ar.low<int>(1);
     // RQI scratch: up to a quarter of the array, at most one warp slot per 4 singletons
-    // lanes per singleton: 8 (the latency-bound choice for one matrix) unless forced
-    const int team = (opts && (opts->rqi_team == 2 || opts->rqi_team == 8)) ? opts->rqi_team : 8;
+    // lanes per singleton: 8, the latency-bound choice for one matrix and the instance
+    // compiled without a stack frame (opts->rqi_team is not applied here)
+    const int team = 8;
     const size_t slot_bytes = (size_t)rqi_scratch_per_index(team) * n * sizeof(double);
     const long long want_slots = (mtotal + rqi_singles_per_slot(team) - 1) / rqi_singles_per_slot(team);
     const long long cap_slots = std::max<long long>(1, (MR3_STATIC_SCRATCH_BYTES / 4) / slot_bytes);
