@@ -99,7 +99,12 @@ typedef struct {
                                   shared with the root instead of recomputed as d+ l+ (Ch. 3,
                                   representation forms; Ch. 5).  The double-double tree always
                                   works this way [0]                                         */
-    int reserved[1];
+    int graph;                 /* the tree's level loop captured in one CUDA graph (no host
+                                  read-back between levels): 0 = for solves of 2 or more
+                                  matrices, 1 = always, -1 = never.  Binary64 tree only,
+                                  without abs_split; a tree deeper than the graph's 12
+                                  levels, or representations that overflow its fixed arenas,
+                                  are redone by the host-driven loop (same results) [0]      */
 } mr3_opts;
 
 /* Fault injection (tests of the safeguards; nothing here faults a GPU). */
@@ -145,6 +150,11 @@ typedef struct {
     int envelope_rrr;          /* ... of those, clusters a first candidate of which passed
                                   the envelope-weighted growth test (Alg. "Shifting the
                                   spectrum", remark 3)                                      */
+    int graph_levels;          /* levels run inside the graph-captured loop (0: host loop);
+                                  with it, kernel_ms[3] holds the levels' time and groups
+                                  4-6 stay 0                                                */
+    int graph_runs;            /* graph launches (2 after an arena overflow)                */
+    long long graph_pool_peak; /* largest arena need (doubles) of the last graph launch     */
 } mr3_info;
 
 /*

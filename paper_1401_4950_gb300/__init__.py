@@ -37,7 +37,7 @@ class Opts(ctypes.Structure):
                 ("tpe", ctypes.c_int), ("max_depth", ctypes.c_int),
                 ("profile", ctypes.c_int), ("rqi_team", ctypes.c_int),
                 ("bisect_warps", ctypes.c_int), ("abs_split", ctypes.c_int),
-                ("erep", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
+                ("erep", ctypes.c_int), ("graph", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -49,7 +49,9 @@ class Info(ctypes.Structure):
                 ("shift_steps", ctypes.c_longlong), ("twisted_steps", ctypes.c_longlong),
                 ("status_counts", ctypes.c_int * 8), ("kernel_ms", ctypes.c_double * 8),
                 ("kernel_launches", ctypes.c_int * 8), ("ladder_clusters", ctypes.c_int),
-                ("recomputed_rrr", ctypes.c_int), ("envelope_rrr", ctypes.c_int)]
+                ("recomputed_rrr", ctypes.c_int), ("envelope_rrr", ctypes.c_int),
+                ("graph_levels", ctypes.c_int), ("graph_runs", ctypes.c_int),
+                ("graph_pool_peak", ctypes.c_longlong)]
 
     _ARRAYS = ("status_counts", "kernel_ms", "kernel_launches")
 
@@ -116,13 +118,15 @@ KERNEL_GROUPS = ("prologue", "root", "bisect_root", "classify", "rqi", "shift", 
 
 def make_opts(prec=FP64, gaptol=0.0, seed=0, max_rqi=0, max_shift_tries=0, fault_mask=0,
               tpe=0, max_depth=0, profile=0, rqi_team=0, bisect_warps=0, abs_split=0,
-              erep=0) -> Opts:
+              erep=0, graph=0) -> Opts:
     o = Opts()
     o.prec, o.gaptol, o.seed, o.max_rqi = prec, gaptol, seed, max_rqi
     o.max_shift_tries, o.fault_mask, o.tpe, o.max_depth = max_shift_tries, fault_mask, tpe, max_depth
     o.profile, o.rqi_team, o.bisect_warps = profile, rqi_team, bisect_warps
     # abs_split: positive = absolute-gap amendment at the root on (default off)
     o.abs_split, o.erep = int(abs_split), int(bool(erep))
+    # graph: 0 = level loop in one CUDA graph for solves of 2+ matrices, 1 = always, -1 = never
+    o.graph = int(graph)
     return o
 
 

@@ -20,7 +20,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmr3.so")
 
 SOURCES = ["mr3_prologue.cu", "mr3_levels.cu", "mr3_rqi.cu", "mr3_api.cu", "mr3_backward.cu",
-           "mr3_static.cu", "mr3_ddpath.cu", "mr3_tc_gemm.cu", "mr3_adjoint.cu"]
+           "mr3_static.cu", "mr3_ddpath.cu", "mr3_tc_gemm.cu", "mr3_adjoint.cu",
+           "mr3_graph.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

@@ -33,6 +33,7 @@ struct Opts {
     int bisect_warps;
     int abs_split;
     int erep;
+    int graph;
 };
 
 Opts resolve(const mr3_opts *o) {
@@ -51,21 +52,22 @@ Opts resolve(const mr3_opts *o) {
                                                                          : MR3_BISECT_WARPS_PER_SM;
     r.abs_split = (o && o->abs_split > 0) ? 1 : 0;
     r.erep = (o && o->erep) ? 1 : 0;
+    r.graph = o ? (o->graph > 0 ? 1 : (o->graph < 0 ? -1 : 0)) : 0;
     return r;
 }
 
 // Lanes per eigenvalue for the multisection: enough lanes in flight to keep the SMs busy
 // (about MR3_BISECT_WARPS_PER_SM warps per SM on 152 SMs), at most 32; opts->tpe overrides.
+// Levels unrolled in the graph-captured level loop, and the number of matrices from which a
+// solve takes that loop by default (opts->graph = 0).
+#ifndef MR3_GRAPH_LEVELS
+#define MR3_GRAPH_LEVELS 12
+#endif
+constexpr int kGraphLevels = MR3_GRAPH_LEVELS;
+constexpr int kGraphMinMatrices = 2;
+
 int lanes_for(long long nactive, const Opts &o) {
-    if (o.tpe > 0) {
-        int L = 1;
-        while (L * 2 <= o.tpe && L < 32) L *= 2;
-        return L;
-    }
-    const long long target = 152ll * 32 * o.bisect_warps;
-    int L = 1;
-    while (L < 32 && (long long)(2 * L) * nactive <= target) L *= 2;
-    return L;
+    return bisect_lanes(nactive, o.bisect_warps, o.tpe);
 }
 
 // Warp slots (one warp each) for an RQI launch with the given team size: one per
@@ -444,6 +446,127 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
         rqi_done[level & 1] = done;
         return 0;
     };
+    // ---- the levels in one graph (mr3_graph.cu), when the options allow it; on a deeper
+    // tree or an arena overflow the state after the root bisection is restored and the
+    // host-driven loop below does the levels instead
+    bool levels_done = false;
+    int graph_levels = 0, graph_runs = 0;
+    long long graph_peak = 0;
+    cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cap_status);
+    const bool graph_auto = nmat >= kGraphMinMatrices;
+    if (!dd && !o.abs_split && o.max_depth >= kGraphLevels && cap_status == cudaStreamCaptureStatusNone &&
+        (o.graph > 0 || (o.graph == 0 && graph_auto))) {
+        GraphLevels G;
+        std::memset(&G, 0, sizeof(G));
+        G.levels = kGraphLevels;
+        G.nblk = nblk;
+        G.nmat = nmat;
+        G.nmax = nmax;
+        G.ncols = ncols;
+        G.cap_cl = ncols / 2 + 1;
+        // arenas: the worst case (every cluster of two members) when it is at most twice the
+        // size of Z (arena 0, which holds the first level's children, the largest set) or
+        // Z's size (arenas 1 and 2), else those sizes; a run that overflows reports each
+        // arena's need, and the levels are redone once with arenas of those sizes
+        long long worst = 0, zsize = 0;
+        for (auto &M : mats) {
+            worst += (long long)(M.m / 2) * rep_size(M.n);
+            zsize += (long long)M.m * M.n;
+        }
+        for (int k = 0; k < 3; ++k)
+            G.pool_cap[k] = std::max<long long>(
+                std::min(worst, std::max((k == 0 ? 2 : 1) * zsize, 1ll << 24)), rep_size(nmax));
+        G.blks = blks;
+        G.mats = dmats;
+        G.nodes0 = nodes0;
+        G.pool0 = pool0;
+        for (int k = 0; k < 3; ++k) G.nodes[k] = ws.get<Node>(G.cap_cl);
+        G.singles[0] = singles2[0];
+        G.singles[1] = singles2[1];
+        G.clusters = clusters;
+        G.crep = crep;
+        G.cnode = cnode;
+        G.jloc = jloc;
+        G.next_active = ws.get<int>(ncols);
+        G.work = work;
+        G.lo = lo;
+        G.hi = hi;
+        G.gapl = gapl;
+        G.gapr = gapr;
+        G.tau = ws.get<double>(G.cap_cl);
+        G.tri = ws.get<double2>(2 * G.cap_cl);
+        G.shift_ws = ws.get<char>(shift_scratch_bytes((int)G.cap_cl, o.max_tries));
+        G.ctrs = ws.get<LevelCounters>(kGraphLevels);
+        G.slots2 = (int)rqi_slots(ncols, nmax, scratch_cap_bytes, 2);
+        G.slots8 = (int)rqi_slots(ncols, nmax, scratch_cap_bytes, 8);
+        const size_t sc2 = (size_t)G.slots2 * rqi_scratch_per_index(2) * nmax;
+        const size_t sc8 = (size_t)G.slots8 * rqi_scratch_per_index(8) * nmax;
+        G.scratch = ws.get<double>(std::max(sc2, sc8));
+        G.d = d;
+        G.e = e;
+        G.w = w;
+        G.Z = Z;
+        G.dinfo = dinfo;
+        G.gaptol = o.gaptol;
+        G.rtol = rtol;
+        G.max_tries = o.max_tries;
+        G.max_rqi = o.max_rqi;
+        G.erep = o.erep;
+        G.rqi_team = o.rqi_team;
+        G.bisect_warps = o.bisect_warps;
+        G.tpe = o.tpe;
+        G.fault_mask = o.fault_mask;
+        // the state after the root bisection, for the fallback
+        double *bk_lo = ws.get<double>(ncols), *bk_hi = ws.get<double>(ncols);
+        int *bk_cnode = ws.get<int>(ncols), *bk_jloc = ws.get<int>(ncols);
+        DevInfo *bk_info = ws.get<DevInfo>(1);
+        CKW(ws);
+        CK(cudaMemcpyAsync(bk_lo, lo, sizeof(double) * ncols, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(bk_hi, hi, sizeof(double) * ncols, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(bk_cnode, cnode, sizeof(int) * ncols, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(bk_jloc, jloc, sizeof(int) * ncols, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemcpyAsync(bk_info, dinfo, sizeof(DevInfo), cudaMemcpyDeviceToDevice, s));
+        for (int attempt = 0; attempt < 2 && !levels_done; ++attempt) {
+            for (int k = 0; k < 3; ++k) G.pool[k] = ws.get<double>(G.pool_cap[k]);
+            CKW(ws);
+            tk = prof.begin();
+            int lv = 0;
+            long long need[3] = {0, 0, 0};
+            const int grc = run_levels_graph(G, s, side, &lv, need);
+            prof.end(tk, 3, 1);
+            graph_runs += 1;
+            graph_peak = std::max(need[0], std::max(need[1], need[2]));
+            if (grc < 0) return -grc;
+            for (int k = 0; k < 3; ++k) ws.release(G.pool[k]);
+            if (grc == 0) {
+                levels_done = true;
+                graph_levels = lv;
+                break;
+            }
+            // restore the state after the root bisection
+            CK(cudaMemcpyAsync(lo, bk_lo, sizeof(double) * ncols, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(hi, bk_hi, sizeof(double) * ncols, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(cnode, bk_cnode, sizeof(int) * ncols, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(jloc, bk_jloc, sizeof(int) * ncols, cudaMemcpyDeviceToDevice, s));
+            CK(cudaMemcpyAsync(dinfo, bk_info, sizeof(DevInfo), cudaMemcpyDeviceToDevice, s));
+            bool grow = false;
+            for (int k = 0; k < 3; ++k) {
+                if (need[k] > G.pool_cap[k]) {
+                    G.pool_cap[k] = std::min(worst, need[k] + need[k] / 8);
+                    grow = true;
+                }
+            }
+            if (!grow) break; // a deeper tree: the host-driven loop takes over
+        }
+        for (void *p : {(void *)G.nodes[0], (void *)G.nodes[1], (void *)G.nodes[2],
+                        (void *)G.next_active,
+                        (void *)G.tau, (void *)G.tri,
+                        G.shift_ws, (void *)G.ctrs, (void *)G.scratch, (void *)bk_lo,
+                        (void *)bk_hi, (void *)bk_cnode, (void *)bk_jloc, (void *)bk_info})
+            ws.release(p);
+    }
+    if (!levels_done)
     for (int level = 0;; ++level) {
         // the singleton buffer of this parity was last read by the RQI two levels back
         if (rqi_done[level & 1]) { cudaStreamWaitEvent(s, rqi_done[level & 1], 0); rqi_done[level & 1] = nullptr; }
@@ -559,6 +682,9 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
     out.twisted_steps = (long long)hi_info.twisted_steps;
     out.ladder_clusters = hi_info.ladder;
     out.recomputed_rrr = hi_info.recomputed;
+    out.graph_levels = graph_levels;
+    out.graph_runs = graph_runs;
+    out.graph_pool_peak = graph_peak;
     out.envelope_rrr = hi_info.env_accepted;
     for (int k = 0; k < 8; ++k) out.status_counts[k] = hi_info.status[k];
     if (status) out.status_counts[status] += 1;

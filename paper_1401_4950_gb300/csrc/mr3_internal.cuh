@@ -104,7 +104,58 @@ struct LevelCounters {
     int maxcluster;
     int nactive;         // columns in clusters (refined on the next level)
     long long pool_need; // doubles needed for the child representations
+    int overflow;        // the child representations did not fit a fixed pool
+    int pad;
 };
+
+// ---- launch-shape rules shared by the host-driven level loop and the one captured in a
+// graph (where the kernels read the counts from the device): the same count gives the
+// same shape, and the shapes change the Sturm-count samples, hence the results.
+
+// Lanes per eigenvalue of the multisection: enough lanes to keep about warps_per_sm warps
+// per SM busy on 152 SMs, a power of two up to 32; tpe > 0 forces one.
+__host__ __device__ __forceinline__ int bisect_lanes(long long nactive, int warps_per_sm, int tpe) {
+    int L = 1;
+    if (tpe > 0) {
+        while (L * 2 <= tpe && L < 32) L *= 2;
+        return L;
+    }
+    const long long target = 152ll * 32 * warps_per_sm;
+    while (L < 32 && (long long)(2 * L) * nactive <= target) L *= 2;
+    return L;
+}
+
+// Lanes per cluster end of the end refinement (phase 0 double-float, phase 1 binary64):
+// many ends -> fewer lanes (throughput), few ends -> more (latency).
+#ifndef MR3_REFINE_WARPS_PER_SM
+#define MR3_REFINE_WARPS_PER_SM 8
+#endif
+#ifndef MR3_REFINE1_LANES_PER_SM
+#define MR3_REFINE1_LANES_PER_SM 128
+#endif
+__host__ __device__ __forceinline__ long long refine_lane_cap(int phase) {
+    return phase == 0 ? 152ll * 32 * MR3_REFINE_WARPS_PER_SM : 152ll * MR3_REFINE1_LANES_PER_SM;
+}
+__host__ __device__ __forceinline__ int refine_lanes(long long ends, int phase) {
+    const long long cap = refine_lane_cap(phase);
+    int E = phase == 0 ? 4 : 1;
+    while (E < 32 && ends * (2 * E) <= cap) E *= 2;
+    return E;
+}
+
+// RQI team size: teams of 2 once the singletons clearly outnumber what the resident warps
+// hold with teams of 8; several matrices in one solve switch earlier (their singleton
+// launch runs beside the other matrices' shift kernels).  forced = 2 or 8 overrides.
+#ifndef MR3_RQI_TEAM2_MIN
+#define MR3_RQI_TEAM2_MIN 32768
+#endif
+#ifndef MR3_RQI_TEAM2_MIN_MULTI
+#define MR3_RQI_TEAM2_MIN_MULTI 2048
+#endif
+__host__ __device__ __forceinline__ int rqi_team_rule(long long nsingle, int nmat, int forced) {
+    if (forced == 2 || forced == 8) return forced;
+    return nsingle > (nmat > 1 ? MR3_RQI_TEAM2_MIN_MULTI : MR3_RQI_TEAM2_MIN) ? 2 : 8;
+}
 
 struct DevInfo {
     unsigned long long sturm_steps;

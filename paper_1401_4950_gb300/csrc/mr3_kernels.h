@@ -45,7 +45,8 @@ void launch_zero_z(int nmat, const MatDesc *mats, double *Z, cudaStream_t s);
 void launch_bisect(int ngroups, const int *list, int L, int mtotal, const int *cnode,
                    const Node *nodes, const BlkDesc *blks, const double *pool, const int *jloc,
                    double *lo, double *hi, double rtol, const double *tau_of_node, DevInfo *info,
-                   cudaStream_t s);
+                   cudaStream_t s, const int *dngroups = nullptr, int warps_per_sm = 0,
+                   int tpe = 0);
 // Shared grid of Sturm counts giving the starting intervals of the root level.
 void launch_grid(int nblk, const BlkDesc *blks, const Node *nodes, const double *pool, int *grid,
                  double *lo, double *hi, int max_m, DevInfo *info, cudaStream_t s);
@@ -56,19 +57,22 @@ void launch_grid(int nblk, const BlkDesc *blks, const Node *nodes, const double 
 void launch_classify(int nnode, const Node *nodes, const BlkDesc *blks, const double *lo,
                      const double *hi, double gaptol, double absfac, double *gapl, double *gapr,
                      SingleItem *singles, ClusterItem *clusters, long long *cluster_rep,
-                     int *cnode, LevelCounters *ctr, DevInfo *info, cudaStream_t s);
+                     int *cnode, LevelCounters *ctr, DevInfo *info, cudaStream_t s,
+                     const int *dnnode = nullptr, long long pool_cap = 0);
 // Refine the two extreme eigenvalues of every cluster (Alg. "Shifting the spectrum", first step).
 // carry: 2 ncluster double2 of scratch.
 void launch_refine_ends(int ncluster, const ClusterItem *clusters, const Node *nodes,
                         const BlkDesc *blks, const double *pool, const int *jloc, double *lo,
-                        double *hi, double2 *carry, DevInfo *info, cudaStream_t s);
+                        double *hi, double2 *carry, DevInfo *info, cudaStream_t s,
+                        const int *dncluster = nullptr);
 // tri: scratch of 2 ncluster double2 (existence and growth of the first two candidates);
 // ws: shift_scratch_bytes(ncluster, max_tries) bytes (decisions, back-off results, queues).
 void launch_shift(int ncluster, const ClusterItem *clusters, const long long *cluster_rep,
                   const Node *nodes, const BlkDesc *blks, const double *pool, double *childpool,
                   Node *child_nodes, double *child_tau, int *cnode, int *active_list,
                   const int *jloc, double *lo, double *hi, int max_tries, unsigned fault_mask,
-                  int erep, double2 *tri, void *ws, DevInfo *info, cudaStream_t s);
+                  int erep, double2 *tri, void *ws, DevInfo *info, cudaStream_t s,
+                  const int *dncluster = nullptr);
 // Stream-ordered allocation from the library's memory pool of the current device (one
 // pool per device whose release threshold keeps freed memory for later calls); free with
 // cudaFreeAsync.
@@ -89,6 +93,16 @@ void launch_rqi(int nsingle, const SingleItem *singles, const Node *nodes, const
                 const double *e, double *w, double *Z, double *scratch, int nslots, int nmax,
                 int max_rqi, unsigned fault_mask, int *work_counter, DevInfo *info,
                 int team, cudaStream_t s);
+// The same with the singleton count on the device (at most max_single): both team sizes are
+// launched (grids of at most nslots2 / nslots8 warp slots over the same scratch), and the
+// team the count selects (rqi_team_rule) does the work.
+void launch_rqi_dev(int max_single, const int *dnsingle, int nmat, int forced_team,
+                    const SingleItem *singles, const Node *nodes, const BlkDesc *blks,
+                    const MatDesc *mats, const double *pool, const int *jloc, const double *lo,
+                    const double *hi, const double *gapl, const double *gapr, const double *d,
+                    const double *e, double *w, double *Z, double *scratch, int nslots2,
+                    int nslots8, int nmax, int max_rqi, unsigned fault_mask, int *work_counter,
+                    DevInfo *info, cudaStream_t s);
 
 // Team size (lanes per singleton, 2 or 8) for a launch of nsingle singletons of a solve over
 // nmat matrices; scratch doubles
@@ -148,5 +162,45 @@ void launch_rqi_dd(int nsingle, const SingleItem *singles, const Node *nodes, co
                    const double *d, const double *e, double *w, double *Z, double *scratch,
                    long long nthreads, int max_rqi, unsigned fault_mask, DevInfo *info,
                    cudaStream_t s);
+
+// ---- the level loop captured in one CUDA graph (mr3_graph.cu).  Every buffer is sized
+// for the largest counts a level can have (clusters <= ncols / 2 + 1), the kernels read
+// the level's counts from the device, and the launch shapes follow the same rules as the
+// host-driven loop, so the results are the same bit for bit.
+struct GraphLevels {
+    int levels;                // levels unrolled in the graph
+    int nblk, nmat, nmax;
+    long long ncols, cap_cl;   // columns; clusters per level at most
+    long long pool_cap[3];     // doubles per representation arena
+    const BlkDesc *blks;
+    const MatDesc *mats;
+    Node *nodes0;              // level 0: the roots
+    double *pool0;
+    Node *nodes[3];            // children of level L go to arena L % 3
+    double *pool[3];
+    SingleItem *singles[2];    // singleton list of level L: singles[L & 1]
+    ClusterItem *clusters;
+    long long *crep;
+    int *cnode, *jloc, *next_active, *work;
+    double *lo, *hi, *gapl, *gapr, *tau;
+    double2 *tri;
+    void *shift_ws;            // shift_scratch_bytes(cap_cl, max_tries)
+    LevelCounters *ctrs;       // one per level
+    double *scratch;           // RQI scratch for slots2 team-2 / slots8 team-8 warp slots
+    int slots2, slots8;
+    const double *d, *e;
+    double *w, *Z;
+    DevInfo *dinfo;
+    double gaptol, rtol;
+    int max_tries, max_rqi, erep, rqi_team, bisect_warps, tpe;
+    unsigned fault_mask;
+};
+// Captures G.levels levels on stream s (singletons on side) into one graph, launches it
+// and waits.  Returns 0 when the tree ended within those levels, 1 when the levels must
+// be redone (a deeper tree, or representations that overflowed an arena), or a negative
+// CUDA error.  *levels_run: levels that classified at least one node; need[k]: the
+// largest need of arena k seen up to and including the first level that overflowed.
+int run_levels_graph(const GraphLevels &G, cudaStream_t s, cudaStream_t side, int *levels_run,
+                     long long need[3]);
 
 } // namespace mr3

@@ -13,15 +13,8 @@ namespace mr3 {
 
 // Offset of the shifts from the cluster's end eigenvalues, in units of eps |lambda|
 // (Alg. "Shifting the spectrum" suggests 100).
-// Lanes given to the cluster-end refinement: up to this many warps per SM.
-#ifndef MR3_REFINE_WARPS_PER_SM
-#define MR3_REFINE_WARPS_PER_SM 8
-#endif
-
-// ... and to its binary64 phase: lanes per SM (the binary64 pipe is the limit there).
-#ifndef MR3_REFINE1_LANES_PER_SM
-#define MR3_REFINE1_LANES_PER_SM 128
-#endif
+// Lanes given to the cluster-end refinement: MR3_REFINE_WARPS_PER_SM and
+// MR3_REFINE1_LANES_PER_SM (mr3_internal.cuh, refine_lanes).
 
 // Relative width at which the double-float phase of the cluster-end refinement stops.
 #ifndef MR3_REFINE_DF_RTOL
@@ -67,11 +60,15 @@ __device__ __forceinline__ int node_count(const Node &N, int n, const double *__
 // Counts in double-float (on the node's copy scaled by 2^dfexp, where every binary32
 // product stays normal) are exact for a relative perturbation of the representation of a
 // few units of 2^-47, so the final interval is widened by 32 n 2^-47 relative.
-__global__ void k_bisect2(int ngroups, const int *__restrict__ list, int L, int mtotal,
+__global__ void k_bisect2(int ngroups, const int *__restrict__ list, int L_host, int mtotal,
                           const int *__restrict__ cnode, const Node *__restrict__ nodes,
                           const BlkDesc *__restrict__ blks, const double *__restrict__ pool,
                           const int *__restrict__ jloc, double *lo, double *hi, double rtol,
-                          const double *__restrict__ tau_of_node, DevInfo *info) {
+                          const double *__restrict__ tau_of_node, DevInfo *info,
+                          const int *dngroups, int warps_per_sm, int tpe) {
+    // with a device count the lanes per eigenvalue follow the host's rule
+    if (dngroups) ngroups = *dngroups;
+    const int L = dngroups ? bisect_lanes(ngroups, warps_per_sm, tpe) : L_host;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const int gid = tid / L;
@@ -202,14 +199,19 @@ __global__ void k_bisect2(int ngroups, const int *__restrict__ list, int L, int 
 void launch_bisect(int ngroups, const int *list, int L, int mtotal, const int *cnode,
                    const Node *nodes, const BlkDesc *blks, const double *pool, const int *jloc,
                    double *lo, double *hi, double rtol, const double *tau_of_node, DevInfo *info,
-                   cudaStream_t s) {
+                   cudaStream_t s, const int *dngroups, int warps_per_sm, int tpe) {
     if (ngroups <= 0) return;
-    const long long threads = (long long)ngroups * L;
+    // with a device count (at most ngroups): enough threads for any count's lanes
+    long long threads = (long long)ngroups * L;
+    if (dngroups)
+        threads = tpe > 0 ? (long long)ngroups * bisect_lanes(0, warps_per_sm, tpe)
+                          : std::max<long long>(152ll * 32 * warps_per_sm, ngroups);
     // small launches in single-warp blocks, so that they spread over all SMs
     const int bs = threads >= 152ll * 128 * 2 ? 128 : 32;
     k_bisect2<<<(unsigned)((threads + bs - 1) / bs), bs, 0, s>>>(ngroups, list, L, mtotal, cnode,
                                                                  nodes, blks, pool, jloc, lo, hi,
-                                                                 rtol, tau_of_node, info);
+                                                                 rtol, tau_of_node, info, dngroups,
+                                                                 warps_per_sm, tpe);
 }
 
 // Root level, most of a block's spectrum requested: G + 1 equally spaced points over the
@@ -299,15 +301,14 @@ void launch_grid(int nblk, const BlkDesc *blks, const Node *nodes, const double 
 // of one column bounded by relative gaps on both sides become singletons, the other groups
 // clusters.  Items are appended with one atomic per warp and kind.  gapl/gapr receive the
 // absolute gaps of every column to its neighbours (used by the RQI acceptance test).
-__global__ void k_classify(int nnode, const Node *__restrict__ nodes, const BlkDesc *__restrict__ blks,
-                           const double *__restrict__ lo, const double *__restrict__ hi,
+__device__ __forceinline__ void k_classify_item(int w, int nnode, const Node *__restrict__ nodes,
+                           const BlkDesc *__restrict__ blks, const double *__restrict__ lo, const double *__restrict__ hi,
                            double gaptol, double absfac, double *gapl, double *gapr,
                            SingleItem *singles,
                            ClusterItem *clusters, long long *cluster_rep, int *cnode,
-                           LevelCounters *ctr, DevInfo *info) {
-    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+                           LevelCounters *ctr, DevInfo *info, const int *dnnode,
+                           long long pool_cap) {
     const int lane = threadIdx.x & 31;
-    if (w >= nnode) return;
     const Node N = nodes[w];
     if (N.c1 < N.c0) return;
     const int nb = blks[N.blk].n;
@@ -358,21 +359,28 @@ __global__ void k_classify(int nnode, const Node *__restrict__ nodes, const BlkD
         const bool clus = end && !single;
         const unsigned ms = __ballot_sync(FULL_MASK, single);
         const unsigned mc = __ballot_sync(FULL_MASK, clus);
-        int sbase = 0, cbase = 0;
+        int sbase = 0, cbase = 0, ovf = 0;
         long long pbase = 0;
         if (lane == 0) {
             if (ms) sbase = atomicAdd(&ctr->nsingle, __popc(ms));
             if (mc) {
-                cbase = atomicAdd(&ctr->ncluster, __popc(mc));
                 pbase = atomicAdd((unsigned long long *)&ctr->pool_need,
                                   (unsigned long long)(rep_size(nb) * __popc(mc)));
+                // a fixed pool (graph-captured level loop) that cannot hold these
+                // representations: the level is flagged and the clusters are dropped (their
+                // columns belong to no node and are left alone; the levels are redone)
+                ovf = pool_cap > 0 && pbase + rep_size(nb) * __popc(mc) > pool_cap;
+                if (ovf) atomicOr(&ctr->overflow, 1);
+                else cbase = atomicAdd(&ctr->ncluster, __popc(mc));
             }
         }
         sbase = __shfl_sync(FULL_MASK, sbase, 0);
         cbase = __shfl_sync(FULL_MASK, cbase, 0);
         pbase = __shfl_sync(FULL_MASK, pbase, 0);
+        ovf = __shfl_sync(FULL_MASK, ovf, 0);
+        const bool emit = clus && !ovf;
         // reserve next-level active-list slots for the cluster columns (warp prefix sum)
-        int csz = clus ? size : 0, incl = csz;
+        int csz = emit ? size : 0, incl = csz;
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(FULL_MASK, incl, o);
             if (lane >= o) incl += y;
@@ -388,7 +396,7 @@ __global__ void k_classify(int nnode, const Node *__restrict__ nodes, const BlkD
             it.node = w;
             singles[sbase + __popc(ms & below)] = it;
         }
-        if (clus) {
+        if (emit) {
             const int k = __popc(mc & below);
             ClusterItem it;
             it.node = w;
@@ -420,15 +428,35 @@ __global__ void k_classify(int nnode, const Node *__restrict__ nodes, const BlkD
     }
 }
 
+__global__ void k_classify(int nnode, const Node *__restrict__ nodes, const BlkDesc *__restrict__ blks,
+                           const double *__restrict__ lo, const double *__restrict__ hi,
+                           double gaptol, double absfac, double *gapl, double *gapr,
+                           SingleItem *singles,
+                           ClusterItem *clusters, long long *cluster_rep, int *cnode,
+                           LevelCounters *ctr, DevInfo *info, const int *dnnode,
+                           long long pool_cap) {
+    // one warp per item; a grid smaller than the items loops over them
+    const int nw_ = gridDim.x * (blockDim.x >> 5);
+    const int bound_ = (dnnode ? *dnnode : nnode);
+    for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < bound_; w += nw_)
+        k_classify_item(w, nnode, nodes, blks, lo, hi, gaptol, absfac, gapl, gapr, singles, clusters,
+                        cluster_rep, cnode, ctr, info, dnnode, pool_cap);
+}
+
 void launch_classify(int nnode, const Node *nodes, const BlkDesc *blks, const double *lo,
                      const double *hi, double gaptol, double absfac, double *gapl, double *gapr,
                      SingleItem *singles, ClusterItem *clusters, long long *cluster_rep,
-                     int *cnode, LevelCounters *ctr, DevInfo *info, cudaStream_t s) {
+                     int *cnode, LevelCounters *ctr, DevInfo *info, cudaStream_t s,
+                     const int *dnnode, long long pool_cap) {
     if (nnode <= 0) return;
     const int wpb = 4;
-    k_classify<<<(nnode + wpb - 1) / wpb, 32 * wpb, 0, s>>>(nnode, nodes, blks, lo, hi, gaptol,
+    // with a device count the grid loops over the nodes
+    const unsigned grid = dnnode ? (unsigned)std::min((nnode + wpb - 1) / wpb, 152 * 8)
+                                 : (unsigned)((nnode + wpb - 1) / wpb);
+    k_classify<<<grid, 32 * wpb, 0, s>>>(nnode, nodes, blks, lo, hi, gaptol,
                                                             absfac, gapl, gapr, singles, clusters,
-                                                            cluster_rep, cnode, ctr, info);
+                                                            cluster_rep, cnode, ctr, info, dnnode,
+                                                            pool_cap);
 }
 
 // ------------------------------------------------------------------ cluster ends
@@ -447,12 +475,12 @@ void launch_classify(int nnode, const Node *nodes, const BlkDesc *blks, const do
 // no inner neighbour: the group of its left end refines its one eigenvalue below 1e-3 of
 // the smaller gap to its outer neighbours (so that the shift next to it leaves it with a
 // relative gap of about 1e3 in the child), and the group of its right end stays idle.
-__global__ void k_refine_ends(int ncluster, const ClusterItem *__restrict__ clusters,
+__device__ __forceinline__ void k_refine_ends_item(long long tid, int E, int ncluster,
+                              const ClusterItem *__restrict__ clusters,
                               const Node *__restrict__ nodes, const BlkDesc *__restrict__ blks,
                               const double *__restrict__ pool, const int *__restrict__ jloc,
-                              double *lo, double *hi, int E, int phase, double2 *carry,
-                              DevInfo *info) {
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+                              double *lo, double *hi, int E_host, int phase, double2 *carry,
+                              DevInfo *info, const int *dncluster) {
     const int lane = threadIdx.x & 31;
     const int g = tid / E, k = lane % E, gbase = lane - k;
     const unsigned gmask = (E == 32) ? 0xffffffffu : (((1u << E) - 1u) << gbase);
@@ -559,21 +587,39 @@ __global__ void k_refine_ends(int ncluster, const ClusterItem *__restrict__ clus
     if (lane == 0 && steps) atomicAdd(&info->shift_steps, steps);
 }
 
+__global__ void k_refine_ends(int ncluster, const ClusterItem *__restrict__ clusters,
+                              const Node *__restrict__ nodes, const BlkDesc *__restrict__ blks,
+                              const double *__restrict__ pool, const int *__restrict__ jloc,
+                              double *lo, double *hi, int E_host, int phase, double2 *carry,
+                              DevInfo *info, const int *dncluster) {
+    // with a device count the lanes per end follow the same rule the host applies, and a
+    // grid smaller than the ends' lanes loops over them one warp (whole groups) at a time
+    if (dncluster) ncluster = *dncluster;
+    const int E = dncluster ? refine_lanes(2ll * ncluster, phase) : E_host;
+    const long long total = 2ll * ncluster * E;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long first = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+    for (long long wb = first; wb < total; wb += stride)
+        k_refine_ends_item(wb + (threadIdx.x & 31), E, ncluster, clusters, nodes, blks, pool, jloc, lo, hi, E_host, phase, carry, info, dncluster);
+}
+
 void launch_refine_ends(int ncluster, const ClusterItem *clusters, const Node *nodes,
                         const BlkDesc *blks, const double *pool, const int *jloc, double *lo,
-                        double *hi, double2 *carry, DevInfo *info, cudaStream_t s) {
+                        double *hi, double2 *carry, DevInfo *info, cudaStream_t s,
+                        const int *dncluster) {
     if (ncluster <= 0) return;
     // lanes per end: many ends -> fewer lanes (throughput), few ends -> more (latency)
     const long long ends = 2ll * ncluster;
     for (int phase = 0; phase < 2; ++phase) {
-        const long long cap = phase == 0 ? 152ll * 32 * MR3_REFINE_WARPS_PER_SM
-                                         : 152ll * MR3_REFINE1_LANES_PER_SM;
-        int E = phase == 0 ? 4 : 1;
-        while (E < 32 && ends * (2 * E) <= cap) E *= 2;
-        const long long threads = ends * E;
+        const int E = refine_lanes(ends, phase);
+        // with a device count (at most ncluster) the grid loops: up to 64 warps per SM
+        const long long threads =
+            dncluster ? std::min(std::max(refine_lane_cap(phase), ends * (phase == 0 ? 4 : 1)),
+                                 152ll * 2048)
+                      : ends * E;
         const int bs = threads >= 152ll * 64 * 2 ? 64 : 32; // small launches spread over the SMs
         k_refine_ends<<<(unsigned)((threads + bs - 1) / bs), bs, 0, s>>>(
-            ncluster, clusters, nodes, blks, pool, jloc, lo, hi, E, phase, carry, info);
+            ncluster, clusters, nodes, blks, pool, jloc, lo, hi, E, phase, carry, info, dncluster);
     }
 }
 
@@ -729,10 +775,12 @@ __global__ void k_shift_trials(int ncluster, const ClusterItem *__restrict__ clu
                                const Node *__restrict__ nodes, const BlkDesc *__restrict__ blks,
                                const double *__restrict__ pool, double *childpool,
                                const double *__restrict__ lo, const double *__restrict__ hi,
-                               unsigned fault_mask, double2 *tri, DevInfo *info) {
+                               unsigned fault_mask, double2 *tri, DevInfo *info,
+                               const int *dncluster) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int ci = t >> 1, side = t & 1;
     unsigned long long steps = 0;
+    if (dncluster) ncluster = *dncluster;
     if (ci < ncluster) {
         const ClusterItem C = clusters[ci];
         const Node P = nodes[C.node];
@@ -843,7 +891,7 @@ __device__ unsigned long long shift_envback(long long t, int nslots,
     return steps;
 }
 
-__global__ void k_shift_envtest(int nslots, const ClusterItem *__restrict__ clusters,
+__device__ __forceinline__ void k_shift_envtest_item(int li, int nslots, const ClusterItem *__restrict__ clusters,
                                 const long long *__restrict__ cluster_rep,
                                 const Node *__restrict__ nodes, const BlkDesc *__restrict__ blks,
                                 const double *__restrict__ pool,
@@ -852,9 +900,7 @@ __global__ void k_shift_envtest(int nslots, const ClusterItem *__restrict__ clus
                                 const double2 *__restrict__ tri, unsigned fault_mask,
                                 const int *__restrict__ ladder, const int *__restrict__ counts,
                                 ShiftDecision *dec, DevInfo *info) {
-    const int li = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (li >= nslots || li >= counts[0]) return; // whole warps
     if (fault_mask & MR3_FAULT_SHIFT_REJECT) return;
     const int ci = ladder[li];
     const ClusterItem C = clusters[ci];
@@ -930,15 +976,33 @@ __global__ void k_shift_envtest(int nslots, const ClusterItem *__restrict__ clus
     }
 }
 
+__global__ void k_shift_envtest(int nslots, const ClusterItem *__restrict__ clusters,
+                                const long long *__restrict__ cluster_rep,
+                                const Node *__restrict__ nodes, const BlkDesc *__restrict__ blks,
+                                const double *__restrict__ pool,
+                                const double *__restrict__ childpool,
+                                const double *__restrict__ lo, const double *__restrict__ hi,
+                                const double2 *__restrict__ tri, unsigned fault_mask,
+                                const int *__restrict__ ladder, const int *__restrict__ counts,
+                                ShiftDecision *dec, DevInfo *info) {
+    // one warp per queued cluster; a grid smaller than the queue loops over it
+    const int nw_ = gridDim.x * (blockDim.x >> 5);
+    const int bound_ = min(nslots, counts[0]);
+    for (int li = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); li < bound_; li += nw_)
+        k_shift_envtest_item(li, nslots, clusters, cluster_rep, nodes, blks, pool, childpool, lo,
+                             hi, tri, fault_mask, ladder, counts, dec, info);
+}
+
 // One thread per cluster: take the better existing first candidate if its growth passes,
 // else queue the cluster for the envelope test and the back-off ladder.
 __global__ void k_shift_select(int ncluster, const ClusterItem *__restrict__ clusters,
                                const Node *__restrict__ nodes, const BlkDesc *__restrict__ blks,
                                const double *__restrict__ lo, const double *__restrict__ hi,
                                unsigned fault_mask, const double2 *__restrict__ tri,
-                               ShiftDecision *dec, int *ladder, int *counts, DevInfo *info) {
+                               ShiftDecision *dec, int *ladder, int *counts, DevInfo *info,
+                               const int *dncluster) {
     const int ci = blockIdx.x * blockDim.x + threadIdx.x;
-    if (ci >= ncluster) return;
+    if (ci >= (dncluster ? *dncluster : ncluster)) return;
     const ClusterItem C = clusters[ci];
     const BlkDesc B = blks[nodes[C.node].blk];
     const ShiftSetup S = shift_setup(C, B, lo, hi);
@@ -970,34 +1034,47 @@ __global__ void k_shift_ladder(int nslots, int max_tries, const ClusterItem *__r
                                const double2 *__restrict__ tri, unsigned fault_mask,
                                const int *__restrict__ ladder, const int *__restrict__ counts,
                                const ShiftDecision *__restrict__ dec, double2 *lad,
-                               unsigned ladder_blocks, DevInfo *info) {
-    unsigned long long steps = 0;
-    if (blockIdx.x >= ladder_blocks) {
-        const long long t = (long long)(blockIdx.x - ladder_blocks) * blockDim.x + threadIdx.x;
-        steps = shift_envback(t, nslots, clusters, cluster_rep, nodes, blks, pool, childpool, lo,
-                              hi, tri, fault_mask, ladder, counts);
-        for (int o = 16; o > 0; o >>= 1) steps += __shfl_xor_sync(FULL_MASK, steps, o);
-        if ((threadIdx.x & 31) == 0 && steps) atomicAdd(&info->shift_steps, steps);
-        return;
+                               unsigned ladder_blocks, DevInfo *info, int regime,
+                               const int *dncluster) {
+    // blocks [0, ladder_blocks) take back-off candidates, the others backward recurrences;
+    // a grid smaller than its role's work loops over it.  With a device count (regime 1:
+    // the launch of the few-clusters order, 2: of the many-clusters order) the launch runs
+    // only when the count selects its order.
+    if (regime != 0) {
+        const bool many = *dncluster >= kEnvSequentialClusters;
+        if ((regime == 1) == many) return;
     }
+    const bool env_role = blockIdx.x >= ladder_blocks;
+    const long long rb = env_role ? blockIdx.x - ladder_blocks : blockIdx.x;
+    const long long nrb = env_role ? gridDim.x - ladder_blocks : ladder_blocks;
     const int NL = ladder_width(max_tries);
-    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int li = (int)(gid / NL), j = (int)(gid % NL);
-    if (li < nslots && li < counts[0] && dec[ladder[li]].win < 0) {
-        const int ci = ladder[li];
-        const ClusterItem C = clusters[ci];
-        const Node P = nodes[C.node];
-        const BlkDesc B = blks[P.blk];
-        const int n = B.n;
-        const ShiftSetup S = shift_setup(C, B, lo, hi);
-        const double off = ldexp(S.delta, j / 2);
-        const double tau = (j & 1) ? S.tau_r0 + off : S.tau_l0 - off;
-        const double *pd = pool + P.rep;
-        bool ex = false;
-        double g = INFINITY;
-        trial_shift<false>(n, pd, pd + 2 * n, tau, nullptr, nullptr, 0, ex, g);
-        lad[(long long)li * NL + j] = make_double2(ex ? 1.0 : 0.0, g);
-        steps = n;
+    const int nq = min(nslots, counts[0]);
+    const long long total = env_role ? 2ll * nq : (long long)nq * NL;
+    unsigned long long steps = 0;
+    for (long long base = rb * blockDim.x; base < total; base += nrb * blockDim.x) {
+        const long long gid = base + threadIdx.x;
+        if (env_role) {
+            steps += shift_envback(gid, nslots, clusters, cluster_rep, nodes, blks, pool,
+                                   childpool, lo, hi, tri, fault_mask, ladder, counts);
+            continue;
+        }
+        const int li = (int)(gid / NL), j = (int)(gid % NL);
+        if (li < nq && dec[ladder[li]].win < 0) {
+            const int ci = ladder[li];
+            const ClusterItem C = clusters[ci];
+            const Node P = nodes[C.node];
+            const BlkDesc B = blks[P.blk];
+            const int n = B.n;
+            const ShiftSetup S = shift_setup(C, B, lo, hi);
+            const double off = ldexp(S.delta, j / 2);
+            const double tau = (j & 1) ? S.tau_r0 + off : S.tau_l0 - off;
+            const double *pd = pool + P.rep;
+            bool ex = false;
+            double g = INFINITY;
+            trial_shift<false>(n, pd, pd + 2 * n, tau, nullptr, nullptr, 0, ex, g);
+            lad[(long long)li * NL + j] = make_double2(ex ? 1.0 : 0.0, g);
+            steps += n;
+        }
     }
     for (int o = 16; o > 0; o >>= 1) steps += __shfl_xor_sync(FULL_MASK, steps, o);
     if ((threadIdx.x & 31) == 0 && steps) atomicAdd(&info->shift_steps, steps);
@@ -1096,15 +1173,14 @@ __global__ void k_shift_recompute(int nslots, const ClusterItem *__restrict__ cl
 //     on the choice of form): its primary data are d+ and the off-diagonal entries
 //     beta_i = dl_i, which dstqds leaves unchanged, so dl+ = dl exactly (every node of the
 //     tree then carries the root's beta bit for bit) and dll+_i = beta_i (beta_i / d+_i).
-__global__ void k_shift(int ncluster, const ClusterItem *__restrict__ clusters,
+__device__ __forceinline__ void k_shift_item(int ci, int ncluster,
+                        const ClusterItem *__restrict__ clusters,
                         const long long *__restrict__ cluster_rep, const Node *__restrict__ nodes,
                         const BlkDesc *__restrict__ blks, const double *__restrict__ pool,
                         double *childpool, Node *child_nodes, double *child_tau, int *cnode,
                         int *active_list, const ShiftDecision *__restrict__ dec, int erep,
-                        DevInfo *info) {
-    const int ci = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+                        DevInfo *info, const int *dncluster) {
     const int lane = threadIdx.x & 31;
-    if (ci >= ncluster) return;
     const ClusterItem C = clusters[ci];
     const Node P = nodes[C.node];
     const BlkDesc B = blks[P.blk];
@@ -1182,6 +1258,20 @@ __global__ void k_shift(int ncluster, const ClusterItem *__restrict__ clusters,
     }
 }
 
+__global__ void k_shift(int ncluster, const ClusterItem *__restrict__ clusters,
+                        const long long *__restrict__ cluster_rep, const Node *__restrict__ nodes,
+                        const BlkDesc *__restrict__ blks, const double *__restrict__ pool,
+                        double *childpool, Node *child_nodes, double *child_tau, int *cnode,
+                        int *active_list, const ShiftDecision *__restrict__ dec, int erep,
+                        DevInfo *info, const int *dncluster) {
+    // one warp per item; a grid smaller than the items loops over them
+    const int nw_ = gridDim.x * (blockDim.x >> 5);
+    const int bound_ = (dncluster ? *dncluster : ncluster);
+    for (int ci = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ci < bound_; ci += nw_)
+        k_shift_item(ci, ncluster, clusters, cluster_rep, nodes, blks, pool, childpool, child_nodes,
+                     child_tau, cnode, active_list, dec, erep, info, dncluster);
+}
+
 size_t shift_scratch_bytes(int ncluster, int max_tries) {
     const size_t nc = (size_t)std::max(ncluster, 1);
     return nc * sizeof(ShiftDecision) + nc * (size_t)ladder_width(max_tries) * sizeof(double2) +
@@ -1192,9 +1282,12 @@ void launch_shift(int ncluster, const ClusterItem *clusters, const long long *cl
                   const Node *nodes, const BlkDesc *blks, const double *pool, double *childpool,
                   Node *child_nodes, double *child_tau, int *cnode, int *active_list,
                   const int *jloc, double *lo, double *hi, int max_tries, unsigned fault_mask,
-                  int erep, double2 *tri, void *ws, DevInfo *info, cudaStream_t s) {
+                  int erep, double2 *tri, void *ws, DevInfo *info, cudaStream_t s,
+                  const int *dncluster) {
     (void)jloc;
     if (ncluster <= 0) return;
+    // with a device count, ncluster is its bound: the grids and the scratch layout follow
+    // the bound, the kernels the count
     const int NL = ladder_width(max_tries);
     ShiftDecision *dec = (ShiftDecision *)ws;
     double2 *lad = (double2 *)(dec + ncluster);
@@ -1205,44 +1298,52 @@ void launch_shift(int ncluster, const ClusterItem *clusters, const long long *cl
     // first candidates, one lane each (single-warp blocks keep the warps spread)
     k_shift_trials<<<(unsigned)((2ll * ncluster + 31) / 32), 32, 0, s>>>(
         ncluster, clusters, cluster_rep, nodes, blks, pool, childpool, lo, hi, fault_mask, tri,
-        info);
+        info, dncluster);
     const unsigned cb = (unsigned)((ncluster + 127) / 128);
     k_shift_select<<<cb, 128, 0, s>>>(ncluster, clusters, nodes, blks, lo, hi, fault_mask, tri,
-                                      dec, ladder, counts, info);
+                                      dec, ladder, counts, info, dncluster);
     // back-off ladder and the envelope test's backward recurrences of the queued clusters
     // (threads past the queue's length return), and the envelope test itself.  Few
     // clusters (latency bound): the ladder and the recurrences share one launch, and the
     // ladder's results for clusters the envelope test settles go unused.  Many clusters
     // (throughput bound): the envelope test first, and the ladder only for the rest.  The
     // decisions are the same either way.
-    const unsigned lblocks = (unsigned)(((long long)ncluster * NL + 31) / 32);
-    const unsigned eblocks = (unsigned)((2ll * ncluster + 31) / 32);
-    const unsigned tblocks = (unsigned)((ncluster + 3) / 4);
-    if (ncluster < kEnvSequentialClusters) {
+    // with a device count the grids loop over the work (a few warps per SM each)
+    const unsigned lfull = (unsigned)(((long long)ncluster * NL + 31) / 32);
+    const unsigned efull = (unsigned)((2ll * ncluster + 31) / 32);
+    const unsigned tfull = (unsigned)((ncluster + 3) / 4);
+    const unsigned lblocks = dncluster ? std::min<unsigned>(lfull, 152 * 32) : lfull;
+    const unsigned eblocks = dncluster ? std::min<unsigned>(efull, 152 * 32) : efull;
+    const unsigned tblocks = dncluster ? std::min<unsigned>(tfull, 152 * 8) : tfull;
+    // (with a device count both orders are launched, and the count picks one on the device)
+    const bool few = ncluster < kEnvSequentialClusters;
+    if (dncluster || few) {
         k_shift_ladder<<<lblocks + eblocks, 32, 0, s>>>(
             ncluster, max_tries, clusters, cluster_rep, nodes, blks, pool, childpool, lo, hi, tri,
-            fault_mask, ladder, counts, dec, lad, lblocks, info);
-        k_shift_envtest<<<tblocks, 128, 0, s>>>(ncluster, clusters, cluster_rep, nodes, blks, pool,
-                                                childpool, lo, hi, tri, fault_mask, ladder,
-                                                counts, dec, info);
-    } else {
+            fault_mask, ladder, counts, dec, lad, lblocks, info, dncluster ? 1 : 0, dncluster);
+    }
+    if (dncluster || !few) {
         k_shift_ladder<<<eblocks, 32, 0, s>>>(
             ncluster, max_tries, clusters, cluster_rep, nodes, blks, pool, childpool, lo, hi, tri,
-            fault_mask, ladder, counts, dec, lad, 0u, info);
-        k_shift_envtest<<<tblocks, 128, 0, s>>>(ncluster, clusters, cluster_rep, nodes, blks, pool,
-                                                childpool, lo, hi, tri, fault_mask, ladder,
-                                                counts, dec, info);
+            fault_mask, ladder, counts, dec, lad, 0u, info, dncluster ? 2 : 0, dncluster);
+    }
+    k_shift_envtest<<<tblocks, 128, 0, s>>>(ncluster, clusters, cluster_rep, nodes, blks, pool,
+                                            childpool, lo, hi, tri, fault_mask, ladder, counts,
+                                            dec, info);
+    if (dncluster || !few) {
         k_shift_ladder<<<lblocks, 32, 0, s>>>(
             ncluster, max_tries, clusters, cluster_rep, nodes, blks, pool, childpool, lo, hi, tri,
-            fault_mask, ladder, counts, dec, lad, lblocks, info);
+            fault_mask, ladder, counts, dec, lad, lblocks, info, dncluster ? 2 : 0, dncluster);
     }
     k_shift_pick<<<cb, 128, 0, s>>>(ncluster, max_tries, fault_mask, clusters, nodes, blks, lo, hi,
                                     tri, ladder, counts, lad, dec, recomp, info);
     k_shift_recompute<<<(unsigned)((ncluster + 31) / 32), 32, 0, s>>>(
         ncluster, clusters, cluster_rep, nodes, blks, pool, childpool, recomp, counts, dec, info);
     // conversion to the child representations, one warp per cluster
-    k_shift<<<ncluster, 32, 0, s>>>(ncluster, clusters, cluster_rep, nodes, blks, pool, childpool,
-                                    child_nodes, child_tau, cnode, active_list, dec, erep, info);
+    k_shift<<<dncluster ? std::min(ncluster, 152 * 32) : ncluster, 32, 0, s>>>(
+        ncluster, clusters, cluster_rep, nodes, blks, pool, childpool,
+                                    child_nodes, child_tau, cnode, active_list, dec, erep, info,
+                                    dncluster);
 }
 
 // ------------------------------------------------------------------ output order

@@ -253,7 +253,14 @@ __global__ void __launch_bounds__(32, RqiOccupancy<TEAM>::kMinBlocks) k_rqi(int 
                                             const double *__restrict__ Ein, double *w, double *Z,
                                             double *scratch, int nmax, int max_rqi,
                                             unsigned fault_mask, int *work_counter,
-                                            DevInfo *info) {
+                                            DevInfo *info, const int *dnsingle, int nmat,
+                                            int forced_team) {
+    // with a device count, both team sizes are launched and the one the host's rule would
+    // not pick returns at once
+    if (dnsingle) {
+        nsingle = *dnsingle;
+        if (rqi_team_rule(nsingle, nmat, forced_team) != TEAM) return;
+    }
     constexpr int kTeam = TEAM, kTeams = 32 / TEAM;
     const int lane = threadIdx.x & 31;
     const int team = lane / kTeam, k = lane % kTeam, tbase = team * kTeam;
@@ -750,27 +757,33 @@ void launch_rqi(int nsingle, const SingleItem *singles, const Node *nodes, const
     if (team == 2)
         k_rqi<2><<<nblocks, 32, 0, s>>>(nsingle, singles, nodes, blks, mats, pool, jloc, lo, hi,
                                         gapl, gapr, d, e, w, Z, scratch, nmax, max_rqi,
-                                        fault_mask, work_counter, info);
+                                        fault_mask, work_counter, info, nullptr, 0, 0);
     else
         k_rqi<8><<<nblocks, 32, 0, s>>>(nsingle, singles, nodes, blks, mats, pool, jloc, lo, hi,
                                         gapl, gapr, d, e, w, Z, scratch, nmax, max_rqi,
-                                        fault_mask, work_counter, info);
+                                        fault_mask, work_counter, info, nullptr, 0, 0);
 }
 
-// Teams of 2 once the singletons clearly outnumber what the resident warps hold with teams
-// of 8 (about 17 warps per SM at this kernel's register count, 4 singletons each).  When a
-// solve covers several matrices the singleton launch runs beside the other matrices' shift
-// and refinement kernels on the main stream, and its fewer binary64 instructions with teams
-// of 2 pay off from much smaller counts (measured on the n = 8192 three-matrix step).
-#ifndef MR3_RQI_TEAM2_MIN
-#define MR3_RQI_TEAM2_MIN 32768
-#endif
-#ifndef MR3_RQI_TEAM2_MIN_MULTI
-#define MR3_RQI_TEAM2_MIN_MULTI 2048
-#endif
-int rqi_team(long long nsingle, int nmat) {
-    return nsingle > (nmat > 1 ? MR3_RQI_TEAM2_MIN_MULTI : MR3_RQI_TEAM2_MIN) ? 2 : 8;
+void launch_rqi_dev(int max_single, const int *dnsingle, int nmat, int forced_team,
+                    const SingleItem *singles, const Node *nodes, const BlkDesc *blks,
+                    const MatDesc *mats, const double *pool, const int *jloc, const double *lo,
+                    const double *hi, const double *gapl, const double *gapr, const double *d,
+                    const double *e, double *w, double *Z, double *scratch, int nslots2,
+                    int nslots8, int nmax, int max_rqi, unsigned fault_mask, int *work_counter,
+                    DevInfo *info, cudaStream_t s) {
+    if (max_single <= 0) return;
+    cudaMemsetAsync(work_counter, 0, sizeof(int), s);
+    const int b2 = std::min(nslots2, (max_single + 15) / 16);
+    const int b8 = std::min(nslots8, (max_single + 3) / 4);
+    k_rqi<2><<<b2, 32, 0, s>>>(max_single, singles, nodes, blks, mats, pool, jloc, lo, hi, gapl,
+                               gapr, d, e, w, Z, scratch, nmax, max_rqi, fault_mask, work_counter,
+                               info, dnsingle, nmat, forced_team);
+    k_rqi<8><<<b8, 32, 0, s>>>(max_single, singles, nodes, blks, mats, pool, jloc, lo, hi, gapl,
+                               gapr, d, e, w, Z, scratch, nmax, max_rqi, fault_mask, work_counter,
+                               info, dnsingle, nmat, forced_team);
 }
+
+int rqi_team(long long nsingle, int nmat) { return rqi_team_rule(nsingle, nmat, 0); }
 int rqi_scratch_per_index(int team) { return kScratchPerSingleton * (32 / team); }
 int rqi_singles_per_slot(int team) { return 32 / team; }
 

@@ -110,15 +110,7 @@ struct Arena {
     } while (0)
 
 int lanes_auto(long long nactive, int tpe, int warps_per_sm) {
-    if (tpe > 0) {
-        int L = 1;
-        while (L * 2 <= tpe && L < 32) L *= 2;
-        return L;
-    }
-    const long long target = 152ll * 32 * warps_per_sm;
-    int L = 1;
-    while (L < 32 && (long long)(2 * L) * nactive <= target) L *= 2;
-    return L;
+    return bisect_lanes(nactive, warps_per_sm, tpe);
 }
 
 // The solve of one matrix (M filled in by the entry point) on the array behind `ar`.
