@@ -101,7 +101,7 @@ typedef struct {
                                   works this way [0]                                         */
     int graph;                 /* the tree's level loop captured in one CUDA graph (no host
                                   read-back between levels): 0 = for solves of 2 or more
-                                  matrices, 1 = always, -1 = never.  Binary64 tree only,
+                                  matrices unless profile is set, 1 = always, -1 = never.  Binary64 tree only,
                                   without abs_split; a tree deeper than the graph's 12
                                   levels, or representations that overflow its fixed arenas,
                                   are redone by the host-driven loop (same results) [0]      */

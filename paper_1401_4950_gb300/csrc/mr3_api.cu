@@ -454,7 +454,9 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
     long long graph_peak = 0;
     cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(s, &cap_status);
-    const bool graph_auto = nmat >= kGraphMinMatrices;
+    // the kernel groups cannot be timed one by one inside a graph: with opts.profile the
+    // default keeps the host-driven loop
+    const bool graph_auto = nmat >= kGraphMinMatrices && !o.profile;
     if (!dd && !o.abs_split && o.max_depth >= kGraphLevels && cap_status == cudaStreamCaptureStatusNone &&
         (o.graph > 0 || (o.graph == 0 && graph_auto))) {
         GraphLevels G;
