@@ -55,8 +55,8 @@ ORACLE_SAMPLE = 256
 # taken on is unchanged: source file, its sha256 prefix at capture time, and the summary
 # under profiles/ that holds the counters.
 # The capture's RQI team size is part of its validity (0: the library's own rule).
-TRAFFIC = {"k_rqi": {"bytes_per_launch": 3.191e9,
-                     "source": "paper_1401_4950_gb300/csrc/mr3_rqi.cu", "sha": "acc7ca48af63b846",
+TRAFFIC = {"k_rqi": {"bytes_per_launch": 3.189e9,
+                     "source": "paper_1401_4950_gb300/csrc/mr3_rqi.cu", "sha": "ac3e79a3631ebebd",
                      "profile": "profiles/k_rqi_traffic_step_n8192.md", "rqi_team": 0}}
 
 CONFIGS = {
