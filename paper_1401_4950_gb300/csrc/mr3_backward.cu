@@ -101,44 +101,110 @@ __global__ void k_apply_F(int n, const double *__restrict__ w, double delta, dou
 // mr3_backward is relative to), one warp: lanes 0-15 and 16-31 bracket lambda_1 and
 // lambda_n by 16-point multisection from the Gershgorin interval with binary64 Sturm
 // counts on T (App. B, NegCount on T; a pivot below pivmin counts as -pivmin).
-__device__ int sturm_T(int n, const double *d, const double *e, double x, double pivmin) {
+// Number of eigenvalues of T below x: the signs of the leading principal minors
+// c_i = (d_i - x) c_{i-1} - e_{i-1}^2 c_{i-2} change once per negative pivot of T - x I
+// (Sturm sequence), with no division on the chain.  The data enter scaled by rs = 1 / s
+// (s the Gershgorin magnitude of T), so that |c_i| grows by at most a factor 3 per step;
+// the pair (c_i, c_{i-1}) is brought back near 1 by a power of two every 8 steps, and an
+// exact zero counts as a negative pivot.
+__device__ int sturm_T(int n, const double *__restrict__ d, const double *__restrict__ e,
+                       double x, double rs) {
     int cnt = 0;
-    double q = d[0] - x;
-    for (int i = 0;; ++i) {
-        if (fabs(q) < pivmin) q = -pivmin;
-        cnt += q < 0.0;
-        if (i == n - 1) break;
-        q = (d[i + 1] - x) - (e[i] * e[i]) / q;
+    double c1 = 1.0, c0 = 0.0;
+    int i = 0;
+    for (; i + 8 <= n; i += 8) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int j = i + u;
+            const double a = (__ldg(d + j) - x) * rs;
+            const double eu = j > 0 ? __ldg(e + j - 1) * rs : 0.0;
+            double c = fma(a, c1, -(eu * eu) * c0);
+            c = (c == 0.0) ? -c1 * 0x1p-80 : c;
+            cnt += (c < 0.0) != (c1 < 0.0);
+            c0 = c1;
+            c1 = c;
+        }
+        const int ex = biased_exp(c1);
+        const double sc = (ex > 0 && ex < 0x7ff) ? pow2i(1023 - ex) : 1.0;
+        c1 *= sc;
+        c0 *= sc;
+    }
+    for (; i < n; ++i) {
+        const double a = (__ldg(d + i) - x) * rs;
+        const double eu = i > 0 ? __ldg(e + i - 1) * rs : 0.0;
+        double c = fma(a, c1, -(eu * eu) * c0);
+        c = (c == 0.0) ? -c1 * 0x1p-80 : c;
+        cnt += (c < 0.0) != (c1 < 0.0);
+        c0 = c1;
+        c1 = c;
     }
     return cnt;
 }
 
-__global__ void k_tnorm(int n, const double *__restrict__ d, const double *__restrict__ e,
-                        double *out) {
-    const int lane = threadIdx.x & 31, half = lane >> 4, kk = lane & 15;
-    double gl = INFINITY, gu = -INFINITY, emax = 0.0;
-    for (int j = 0; j < n; ++j) {
+// ||T|| = max(|lambda_1|, |lambda_n|) by multisection of both extreme eigenvalues, spread
+// over many blocks: st holds {L, H} of each end and the scale; a sweep counts at P points of
+// each bracket (k_tnorm_count) and one thread moves the brackets (k_tnorm_update).
+constexpr int kTnormPoints = 2048; // points per end and sweep (64 single-warp blocks)
+constexpr int kTnormSweeps = 4;    // 11 bits per sweep: 2^-44 of the Gershgorin width
+
+__global__ void k_tnorm_init(int n, const double *__restrict__ d, const double *__restrict__ e,
+                             double *st, int *tcnt) {
+    __shared__ double s_lo[256], s_hi[256];
+    double gl = INFINITY, gu = -INFINITY;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
         const double r = (j > 0 ? fabs(e[j - 1]) : 0.0) + (j < n - 1 ? fabs(e[j]) : 0.0);
         gl = fmin(gl, d[j] - r);
         gu = fmax(gu, d[j] + r);
-        if (j < n - 1) emax = fmax(emax, e[j] * e[j]);
     }
-    const double pivmin = kSafmin * fmax(1.0, emax);
-    const int target = half ? n : 1; // the count reaches target just above the eigenvalue
-    double L = gl, H = gu;
-    for (int sweep = 0; sweep < 16; ++sweep) {
-        const double x = L + (kk + 1) * ((H - L) / 17.0);
-        const unsigned bal = __ballot_sync(0xffffffffu, sturm_T(n, d, e, x, pivmin) < target);
-        const unsigned hm = (bal >> (16 * half)) & 0xffffu;
-        const int t = __popc(hm);
-        const double xl = __shfl_sync(0xffffffffu, x, 16 * half + (t > 0 ? t - 1 : 0));
-        const double xh = __shfl_sync(0xffffffffu, x, 16 * half + (t < 16 ? t : 15));
-        if (t > 0) L = xl;
-        if (t < 16) H = xh;
+    s_lo[threadIdx.x] = gl;
+    s_hi[threadIdx.x] = gu;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            s_lo[threadIdx.x] = fmin(s_lo[threadIdx.x], s_lo[threadIdx.x + o]);
+            s_hi[threadIdx.x] = fmax(s_hi[threadIdx.x], s_hi[threadIdx.x + o]);
+        }
+        __syncthreads();
     }
-    const double l1 = __shfl_sync(0xffffffffu, 0.5 * (L + H), 0);
-    const double ln = __shfl_sync(0xffffffffu, 0.5 * (L + H), 16);
-    if (lane == 0) *out = fmax(fabs(l1), fabs(ln));
+    if (threadIdx.x == 0) {
+        st[0] = st[2] = s_lo[0];
+        st[1] = st[3] = s_hi[0];
+        const double gs = fmax(fabs(s_lo[0]), fabs(s_hi[0]));
+        st[4] = gs > 0.0 ? 1.0 / gs : 1.0;
+        tcnt[0] = tcnt[1] = 0;
+    }
+}
+
+__device__ __forceinline__ double tnorm_point(double L, double H, int p) {
+    return L + (double)(p + 1) * ((H - L) / (double)(kTnormPoints + 1));
+}
+
+// blockIdx.y = 0: the lowest eigenvalue (count < 1 below it), 1: the highest (count < n)
+__global__ void k_tnorm_count(int n, const double *__restrict__ d, const double *__restrict__ e,
+                              const double *__restrict__ st, int *tcnt) {
+    const int end = blockIdx.y;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const double L = st[2 * end], H = st[2 * end + 1];
+    bool below = false;
+    if (p < kTnormPoints) below = sturm_T(n, d, e, tnorm_point(L, H, p), st[4]) < (end ? n : 1);
+    const unsigned b = __ballot_sync(0xffffffffu, below);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(tcnt + end, __popc(b));
+}
+
+__global__ void k_tnorm_update(double *st, int *tcnt, double *out, int last) {
+    if (threadIdx.x != 0) return;
+    double mid[2];
+    for (int end = 0; end < 2; ++end) {
+        const double L = st[2 * end], H = st[2 * end + 1];
+        const int t = tcnt[end]; // points below the eigenvalue
+        const double nl = t > 0 ? tnorm_point(L, H, t - 1) : L;
+        const double nh = t < kTnormPoints ? tnorm_point(L, H, t) : H;
+        st[2 * end] = nl;
+        st[2 * end + 1] = nh;
+        tcnt[end] = 0;
+        mid[end] = 0.5 * (nl + nh);
+    }
+    if (last) *out = fmax(fabs(mid[0]), fabs(mid[1]));
 }
 
 // ---- Ozaki splitting
@@ -542,7 +608,7 @@ extern "C" int mr3_backward_solve(int n, int k, const double *d, const double *e
     };
     if (lib_malloc_async((void **)&part, sizeof(double) * 2 * kRowChunks * (size_t)n, s) != cudaSuccess ||
         (vec && lib_malloc_async((void **)&Y, sizeof(double) * (size_t)n * k, s) != cudaSuccess) ||
-        (vec && lib_malloc_async((void **)&scr, sizeof(double) * 3 * (size_t)n * k, s) != cudaSuccess)) {
+        (vec && lib_malloc_async((void **)&scr, sizeof(double) * adjoint_scratch_doubles(n, k), s) != cudaSuccess)) {
         cudaGetLastError();
         return done(MR3_EOOM);
     }
@@ -558,16 +624,30 @@ extern "C" int mr3_backward_solve(int n, int k, const double *d, const double *e
             return done(MR3_ECUDA);
     }
     if (vec) {
-        // ||T|| = max |lambda| of T (16 sweeps of 16-point multisection: 2^-64 of the
-        // Gershgorin width, far below what delta needs)
-        double hd[1];
+        // ||T|| = max |lambda| of T: the ends of w when all eigenpairs are given (as the
+        // dense path takes it), else by bisection of T's extreme eigenvalues
+        double hd[2] = {0.0, 0.0};
         int rc = 0;
-        double *gmax = nullptr;
-        if (lib_malloc_async((void **)&gmax, sizeof(double), s) != cudaSuccess) { cudaGetLastError(); return done(MR3_EOOM); }
-        k_tnorm<<<1, 32, 0, s>>>(n, d, e, gmax);
-        if (read_back(hd, gmax, sizeof(double), s) != cudaSuccess) rc = MR3_ECUDA;
-        cudaFreeAsync(gmax, s);
-        if (rc) return done(rc);
+        if (k == n) {
+            if (read_back(hd, w, sizeof(double), s) != cudaSuccess ||
+                read_back(hd + 1, w + (k - 1), sizeof(double), s) != cudaSuccess)
+                return done(MR3_ECUDA);
+            hd[0] = std::max(std::fabs(hd[0]), std::fabs(hd[1]));
+        } else {
+            double *gmax = nullptr;
+            if (lib_malloc_async((void **)&gmax, sizeof(double) * 8, s) != cudaSuccess) { cudaGetLastError(); return done(MR3_EOOM); }
+            double *st = gmax + 1;
+            int *tcnt = (int *)(gmax + 6);
+            k_tnorm_init<<<1, 256, 0, s>>>(n, d, e, st, tcnt);
+            for (int sw = 0; sw < kTnormSweeps; ++sw) {
+                // one warp per block: the counts' binary64 instructions spread over the SMs
+                k_tnorm_count<<<dim3(kTnormPoints / 32, 2), 32, 0, s>>>(n, d, e, st, tcnt);
+                k_tnorm_update<<<1, 32, 0, s>>>(st, tcnt, gmax, sw == kTnormSweeps - 1);
+            }
+            if (read_back(hd, gmax, sizeof(double), s) != cudaSuccess) rc = MR3_ECUDA;
+            cudaFreeAsync(gmax, s);
+            if (rc) return done(rc);
+        }
         const double tnorm = hd[0] > 0.0 ? hd[0] : 1.0;
         launch_adjoint(n, k, d, e, w, Z, ldz, gZ, ldgz, tnorm, scr, Y, s);
         k_row_dots<1><<<rgrid, 256, 0, s>>>(n, k, Y, n, Z, ldz, nullptr, pd, pe);

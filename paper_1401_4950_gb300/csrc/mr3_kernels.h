@@ -137,7 +137,9 @@ int tc_gemm_bf16(int M, int N, int K, int k0, int k1, const unsigned short *A, i
                  const unsigned short *B, int ldb, float *C, int ldc, int *err, cudaStream_t s);
 cudaError_t preload_tc_gemm();
 // Eigenvector part of the backward pass one eigenpair at a time (mr3_adjoint.cu): column c
-// of Y (n x k, ld n) such that Y Z^T is the eigenvector part of Tbar; scratch 3 n k doubles.
+// of Y (n x k, ld n) such that Y Z^T is the eigenvector part of Tbar; scratch of
+// adjoint_scratch_doubles(n, k) doubles.
+size_t adjoint_scratch_doubles(int n, int k);
 void launch_adjoint(int n, int k, const double *d, const double *e, const double *w,
                     const double *Z, int ldz, const double *G, int ldg, double tnorm,
                     double *scratch, double *Y, cudaStream_t s);
