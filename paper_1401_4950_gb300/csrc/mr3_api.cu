@@ -3,7 +3,9 @@
 // breadth first: per level classify, singletons by RQI, clusters by a shift and a
 // refinement on the child representation).
 #include <algorithm>
+#include <cstddef>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -117,6 +119,34 @@ struct Prof {
     }
     ~Prof() {
         for (auto e : evs) cudaEventDestroy(e);
+    }
+};
+
+// MR3_TRACE set (and not "0") in the environment: the host-driven level loop prints one
+// line per tree level on stderr: singletons, clusters, the largest cluster, the columns to
+// refine, the stream times of the level's cluster-end refinement, shift and child
+// bisection (event pairs on the main stream; the singletons run beside them), and the
+// sweep statistics of its multisection launches.  Diagnostic only: it synchronises the
+// stream once per level.
+bool trace_on() {
+    static const bool v = [] {
+        const char *t = std::getenv("MR3_TRACE");
+        return t && *t && std::strcmp(t, "0") != 0;
+    }();
+    return v;
+}
+
+struct TraceLevel {
+    int level;
+    LevelCounters hc;
+    cudaEvent_t ev[4];
+    DevInfo sweeps; // the multisection statistics of the level's launches
+};
+struct TraceLog : std::vector<TraceLevel> {
+    ~TraceLog() {
+        for (auto &t : *this)
+            for (auto ev : t.ev)
+                if (ev) cudaEventDestroy(ev);
     }
 };
 
@@ -450,6 +480,7 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
     // tree or an arena overflow the state after the root bisection is restored and the
     // host-driven loop below does the levels instead
     bool levels_done = false;
+    TraceLog trace;
     int graph_levels = 0, graph_runs = 0;
     long long graph_peak = 0;
     cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
@@ -596,8 +627,20 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
         char *shift_ws = ws.get<char>(shift_scratch_bytes(hc.ncluster, o.max_tries));
         int *next_active = ws.get<int>(hc.nactive);
         CKW(ws);
+        TraceLevel *tl = nullptr;
+        if (trace_on()) {
+            trace.push_back(TraceLevel{level, hc, {}, {}});
+            tl = &trace.back();
+            for (auto &ev : tl->ev) cudaEventCreate(&ev);
+            const int one = 1;
+            CK(cudaMemcpyAsync(&dinfo->trace, &one, sizeof(int), cudaMemcpyHostToDevice, s));
+            CK(cudaMemsetAsync(&dinfo->tr_max, 0,
+                               sizeof(DevInfo) - offsetof(DevInfo, tr_max), s));
+            cudaEventRecord(tl->ev[0], s);
+        }
         tk = prof.begin();
         launch_refine_ends(hc.ncluster, clusters, cur_nodes, blks, cur_pool, jloc, lo, hi, tri, dinfo, s);
+        if (tl) cudaEventRecord(tl->ev[1], s);
         launch_shift(hc.ncluster, clusters, crep, cur_nodes, blks, cur_pool, next_pool,
                      next_nodes, tau, cnode, next_active, jloc, lo, hi, o.max_tries, o.fault_mask,
                      o.erep, tri, shift_ws, dinfo, s);
@@ -605,10 +648,18 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
             launch_shift_dd(hc.ncluster, clusters, crep, cur_nodes, blks, cur_pool, cur_lo, next_pool,
                             next_lo, next_nodes, tau, dinfo, s);
         prof.end(tk, 5, dd ? 9 : 8); // refine_ends x2, six shift kernels (+ double-double recompute)
+        if (tl) cudaEventRecord(tl->ev[2], s);
         tk = prof.begin();
         launch_bisect(hc.nactive, next_active, lanes_for(hc.nactive, o), (int)ncols, cnode,
                       next_nodes, blks, next_pool, jloc, lo, hi, rtol, tau, dinfo, s);
         prof.end(tk, 6, 1);
+        if (tl) {
+            cudaEventRecord(tl->ev[3], s);
+            CK(read_back(&tl->sweeps, dinfo, sizeof(DevInfo), s));
+            const int zero = 0;
+            CK(cudaMemcpyAsync(&dinfo->trace, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
+            CK(cudaStreamSynchronize(s));
+        }
         ws.release(next_active);
         ws.release(tri);
         ws.release(shift_ws);
@@ -681,6 +732,26 @@ int solve(int nmat, std::vector<MatDesc> &mats, long long nrows, long long ncols
     out.sturm_steps = (long long)hi_info.sturm_steps;
     out.shift_steps = (long long)hi_info.shift_steps;
     prof.collect(out);
+    for (auto &t : trace) {
+        float ms[3] = {0.f, 0.f, 0.f};
+        for (int k = 0; k < 3; ++k) cudaEventElapsedTime(&ms[k], t.ev[k], t.ev[k + 1]);
+        std::fprintf(stderr,
+                     "mr3 level %d: singletons %d clusters %d largest %d refine %d pool %lld | "
+                     "ends %.3f ms shift %.3f ms bisect %.3f ms\n",
+                     t.level, t.hc.nsingle, t.hc.ncluster, t.hc.maxcluster, t.hc.nactive,
+                     t.hc.pool_need, ms[0], ms[1], ms[2]);
+        static const char *kind[3] = {"bisect", "ends/df", "ends/fp64"};
+        for (int k = 0; k < 3; ++k) {
+            const DevInfo &v = t.sweeps;
+            if (!v.tr_items[k]) continue;
+            std::fprintf(stderr, "    %-9s items %llu sweeps mean %.2f max %d lane use %.3f\n",
+                         kind[k], v.tr_items[k], (double)v.tr_sweeps[k] / (double)v.tr_items[k],
+                         v.tr_max[k],
+                         v.tr_warp_lanes[k]
+                             ? (double)v.tr_lane_counts[k] / (double)v.tr_warp_lanes[k]
+                             : 0.0);
+        }
+    }
     out.twisted_steps = (long long)hi_info.twisted_steps;
     out.ladder_clusters = hi_info.ladder;
     out.recomputed_rrr = hi_info.recomputed;

@@ -173,7 +173,31 @@ struct DevInfo {
     int ladder;       // clusters whose first two shift candidates failed the plain test
     int recomputed;   // ... of which a back-off candidate passed the growth test
     int env_accepted; // ... of which a first candidate passed the envelope test
+    // multisection statistics, gathered only while trace is nonzero: [0] the bisection,
+    // [1] and [2] the two phases of the cluster-end refinement.  Per launch: the items,
+    // their sweeps (sum and maximum), and the lanes that counted over the lanes of the
+    // warps' sweeps (the lane utilisation)
+    int trace;
+    int tr_max[3];
+    unsigned long long tr_items[3], tr_sweeps[3], tr_lane_counts[3], tr_warp_lanes[3];
 };
+
+// Adds one warp's multisection statistics (all 32 lanes call it): sw counts of this lane,
+// rounds the warp ran, group leaders (lead) add their item with its sweeps.
+__device__ __forceinline__ void trace_sweeps(DevInfo *info, int kind, bool lead, int sw,
+                                             int rounds) {
+    unsigned long long c = (unsigned long long)sw;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lead && sw > 0) {
+        atomicAdd(&info->tr_items[kind], 1ull);
+        atomicAdd(&info->tr_sweeps[kind], (unsigned long long)sw);
+        atomicMax(&info->tr_max[kind], sw);
+    }
+    if ((threadIdx.x & 31) == 0 && c) {
+        atomicAdd(&info->tr_lane_counts[kind], c);
+        atomicAdd(&info->tr_warp_lanes[kind], 32ull * (unsigned long long)rounds);
+    }
+}
 
 // ------------------------------------------------------------------ bit helpers
 

@@ -149,6 +149,7 @@ __global__ void k_bisect2(int ngroups, const int *__restrict__ list, int L_host,
     const double kap = 32.0 * n * 0x1p-47;
     bool used_df = false;
     bool df_phase = N.dfok != 0;
+    int sw = 0, rounds = 0;
     for (int sweep = 0; sweep < 400; ++sweep) {
         if (active && df_phase && h - l <= 2.0 * kap * fmax(fabs(l), fabs(h))) {
             if (used_df) {
@@ -173,7 +174,9 @@ __global__ void k_bisect2(int ngroups, const int *__restrict__ list, int L_host,
                 cnt = negcount_ldl(n, rep, rep + 2 * n, x);
             }
             steps += n;
+            ++sw;
         }
+        ++rounds;
         const unsigned bal = __ballot_sync(0xffffffffu, cnt < j);
         const int t = __popc(bal & gmask);
         const double xl = __shfl_sync(0xffffffffu, x, gbase + (t > 0 ? t - 1 : 0));
@@ -183,6 +186,7 @@ __global__ void k_bisect2(int ngroups, const int *__restrict__ list, int L_host,
             if (t < L) h = xh;
         }
     }
+    if (info->trace) trace_sweeps(info, 0, active && k == 0, sw, rounds);
     const bool grp_df = (__ballot_sync(0xffffffffu, used_df) & gmask) != 0;
     if (active && k == 0) {
         if (grp_df) {
@@ -547,6 +551,7 @@ __device__ __forceinline__ void k_refine_ends_item(long long tid, int E, int ncl
             }
         }
     }
+    int sw = 0, rounds = 0;
     for (int sweep = 0; sweep < 64; ++sweep) {
         const double w = H - L;
         const double gap_lb = side ? (L - nb) : (nb - H);
@@ -560,7 +565,9 @@ __device__ __forceinline__ void k_refine_ends_item(long long tid, int E, int ncl
         if (!done) {
             cnt = (phase == 0) ? node_count(P, n, pd, x) : negcount_ldl(n, pd, pd + 2 * n, x);
             steps += n;
+            ++sw;
         }
+        ++rounds;
         const unsigned bal = __ballot_sync(0xffffffffu, cnt < tgt);
         const int t = __popc(bal & gmask);
         const double xl = __shfl_sync(0xffffffffu, x, gbase + (t > 0 ? t - 1 : 0));
@@ -578,6 +585,7 @@ __device__ __forceinline__ void k_refine_ends_item(long long tid, int E, int ncl
             if (t < E) H = xh;
         }
     }
+    if (info->trace) trace_sweeps(info, 1 + phase, active && k == 0, sw, rounds);
     if (active && k == 0) {
         lo[col] = L;
         hi[col] = H;
