@@ -75,7 +75,13 @@ typedef struct {
     int tpe;                   /* bisection lanes per eigenvalue: 0 = auto, else 1..32       */
     int max_depth;             /* cap on the representation-tree depth [64]                  */
     int profile;               /* nonzero: time each kernel group with CUDA events on the
-                                  call's stream and report it in mr3_info.kernel_ms [0]        */
+                                  call's stream and report it in mr3_info.kernel_ms [0].
+                                  Diagnostics: with MR3_TRACE=1 in the environment the
+                                  host-driven level loop also prints one line per tree level
+                                  on stderr (counts, main-stream times of the level's cluster
+                                  ends, shifts and child bisection, and the sweep statistics
+                                  of its multisection launches); it synchronises the stream
+                                  once per level                                             */
     int rqi_team;              /* lanes per singleton in the RQI: 0 = auto (2 for many
                                   singletons, else 8), 2 or 8 to force one; mr3_stemr_static
                                   always uses 8 [0]                                          */
