@@ -1,10 +1,11 @@
 """Exact-arithmetic pins of the thesis' factorization algorithms and of the division-free
 forms the kernels run them in.
 
-Everything here is rational arithmetic (fractions.Fraction) on small random inputs, so an
-identity either holds exactly or the test fails; no tolerance is involved.  The checks are
-against plain definitions: the product of the computed factors, the inverse of the shifted
-matrix, and Sylvester's law of inertia.
+The identities are checked in rational arithmetic (fractions.Fraction) on small random
+inputs, so each either holds exactly or the test fails; no tolerance is involved.  The
+checks are against plain definitions: the product of the computed factors, the inverse of
+the shifted matrix, and Sylvester's law of inertia.  The last pin, an inequality, runs in
+binary64 against LAPACK's eigenvectors.
 
 * Alg. dstqds (Ch. 3, "Eigenvectors of symmetric tridiagonals"): L+ D+ L+^T = L D L^T - tau I.
 * Alg. dqds, same section.  Its printed loop assigns the new pivot to u-(i+1) and carries a
@@ -22,6 +23,9 @@ matrix, and Sylvester's law of inertia.
   the envelope test runs dqds backwards as p_k = N_k / M_k with M_k = N + dll_k M,
   N_k = (d_k - tau) N - tau dll_k M.  Both forms equal the quotient forms exactly, and the
   number of sign changes of c is the number of eigenvalues below sigma.
+* The envelope bound of the shift's second test (a reading of Alg. "Shifting the spectrum",
+  whose envelope test has no formula in the thesis): the weight of a group of eigenvectors
+  at index k is at most Lambda (1/|gamma_k| + 1/g).
 """
 from fractions import Fraction as F
 import random
@@ -232,3 +236,45 @@ def test_sign_changes_count_the_eigenvalues_below_sigma(case):
             cp = c
         else:
             assert cnt == int(np.sum(lam < float(sigma)))
+
+
+def _envelope_case(seed):
+    rng = np.random.default_rng(1000 + seed)
+    n = 40
+    dT = rng.uniform(-1, 1, n)
+    eT = rng.uniform(-1, 1, n - 1)
+    T = np.diag(dT) + np.diag(eT, 1) + np.diag(eT, -1)
+    lam, Z = np.linalg.eigh(T)
+    j0 = int(rng.integers(2, n - 12))
+    j1 = j0 + int(rng.integers(1, 8))
+    if seed % 2 == 0:  # shift left of the group
+        tau = lam[j0] - 1e-3 * (lam[j0] - lam[j0 - 1])
+        Lam = lam[j1] - tau
+    else:  # right of it
+        tau = lam[j1] + 1e-3 * (lam[j1 + 1] - lam[j1])
+        Lam = tau - lam[j0]
+    outside = np.r_[lam[:j0], lam[j1 + 1:]]
+    g = np.min(np.abs(outside - tau))
+    gamma = 1.0 / np.diag(np.linalg.inv(T - tau * np.eye(n)))
+    env2 = np.sum(Z[:, j0:j1 + 1] ** 2, axis=1)
+    return env2, gamma, Lam, g
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_envelope_bound_of_the_shift_test(seed):
+    # The envelope bound the shift's second test uses (a reading: the thesis names an
+    # envelope test without a formula).  With mu_j = lambda_j - tau,
+    # 1/gamma_k = sum_j z_j(k)^2 / mu_j; the group's mu_j share one sign and are at most
+    # Lambda in magnitude, the others at least g, so
+    # env2(k) = sum_{j in group} z_j(k)^2 <= Lambda (1/|gamma_k| + 1/g).
+    env2, gamma, Lam, g = _envelope_case(seed)
+    assert np.all(env2 <= Lam * (1.0 / np.abs(gamma) + 1.0 / g) * (1 + 1e-8))
+
+
+def test_envelope_bound_needs_the_outside_term():
+    # a planted mistake: without the outside eigenvalues' term 1/g the bound fails
+    violated = 0
+    for seed in range(6):
+        env2, gamma, Lam, g = _envelope_case(seed)
+        violated += int(np.any(env2 > Lam / np.abs(gamma) * (1 + 1e-8)))
+    assert violated > 0
