@@ -407,7 +407,12 @@ def run_gpu(args, cfg, rank, world):
 
     # ---- end to end through the C ABI on host buffers: every step is one
     # mr3_stemr_batched_host call, which copies d and e in from pinned host memory, solves,
-    # and copies w and Z back into pinned host memory before returning
+    # and copies w and Z back into pinned host memory before returning.  The library's
+    # memory pool is handed back to the driver first, so that these calls find the pool a
+    # fresh process has after its first call, not the blocks the launch-shape tuning and
+    # the headline steps left in it.
+    torch.cuda.synchronize()
+    mr3.release_memory()
     dh = torch.tensor(dcat_h).pin_memory()
     eh = torch.tensor(ecat_h).pin_memory()
     zlen = int(sum(n * n for n in sizes))
